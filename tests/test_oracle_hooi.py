@@ -1,0 +1,157 @@
+"""Pins for the oracle's MACH-HOSVD / MACH-HOOI (Algorithm 1 / Algorithm 2)
+against what the paper and the mathematics fix: the closed-form exactness of
+HOSVD on noise-free data of exact multilinear rank (Section 2.1 "Tucker3
+Algorithms"), the p = 1 special case (X^ = X) reducing to plain HOOI computed
+by an independent brute-force route, orthonormal factors, the projection
+bound ||G|| <= ||X^|| and HOOI's monotone fit, stationarity at convergence,
+and the 1/p reweighing of Algorithm 2."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mach_oracle as O
+from paper_0909_4969_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def brute_hooi(X, ranks, sweeps):
+    """Plain HOOI written independently: Kronecker-form TTM chain
+    Y_(n) = X_(n) (kron of the other factors) and dense SVDs."""
+    d = X.ndim
+    A = [O.leading_left_singular_vectors(O.unfold(X, k), ranks[k]) for k in range(d)]
+    for _ in range(sweeps):
+        for n in range(d):
+            K = None
+            for k in range(d):
+                if k == n:
+                    continue
+                K = A[k] if K is None else np.kron(A[k], K)
+            A[n] = O.leading_left_singular_vectors(O.unfold(X, n) @ K, ranks[n])
+    G = X
+    for k in range(d):
+        G = O.mode_product(G, A[k].T, k)
+    return G, A
+
+
+def exact_rank_tensor(dims, ranks, seed):
+    X, G, Us = synth.tucker_numpy(synth.TuckerSpec(dims, ranks, "gaussian", 0.0, seed, "float64"))
+    return X, Us
+
+
+@pytest.mark.parametrize("dims,ranks", [((8, 7, 9), (3, 2, 4)), ((6, 5, 7, 4), (2, 3, 2, 2))])
+def test_hosvd_exact_on_exact_multilinear_rank(dims, ranks):
+    X, Us = exact_rank_tensor(dims, ranks, 1)
+    S, G, A = O.mach_hosvd(X, ranks, 1.0, 0)
+    assert S.idx.size == X.size
+    assert O.relative_error(X, G, A) < 1e-13
+    for k in range(len(dims)):
+        assert O.subspace_distance(A[k], Us[k]) < 1e-12
+
+
+@pytest.mark.parametrize("dims,ranks", [((4, 3, 5), (2, 2, 3)), ((6, 5, 7, 3), (2, 3, 2, 2)), ((9, 8, 10), (3, 3, 3))])
+def test_p_one_reduces_to_plain_hooi(dims, ranks):
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal(dims)
+    S, G, A = O.mach_hooi(X, ranks, 1.0, 5, sweeps=4)
+    Gb, Ab = brute_hooi(X, list(ranks), 4)
+    for k in range(len(dims)):
+        assert O.subspace_distance(A[k], Ab[k]) < 1e-10
+    Af = [O.fix_signs(a) for a in A]
+    Abf = [O.fix_signs(a) for a in Ab]
+    Gf = S.dense(scaled=True)
+    Gbf = X
+    for k in range(len(dims)):
+        Gf = O.mode_product(Gf, Af[k].T, k)
+        Gbf = O.mode_product(Gbf, Abf[k].T, k)
+    np.testing.assert_allclose(Gf, Gbf, rtol=1e-9, atol=1e-10 * O.norm(X))
+
+
+def _c1_small():
+    spec = synth.TuckerSpec((30, 20, 40), (3, 3, 3), "gaussian", 0.1, 3, "float64")
+    X, _, Us = synth.tucker_numpy(spec)
+    return X, Us
+
+
+def test_invariants_orthonormal_projection_monotone():
+    X, _ = _c1_small()
+    idx, vals = O.sample(X, 0.3, 4)
+    S = O.SampledTensor(X.shape, idx, vals, 0.3)
+    hist = []
+    G, A = O.hooi(S, (3, 3, 3), 6, history=hist)
+    for a in A:
+        assert np.max(np.abs(a.T @ a - np.eye(a.shape[1]))) < 1e-13
+    assert O.norm(G) <= O.norm(S.dense(scaled=True)) * (1 + 1e-14)
+    for a, b in zip(hist, hist[1:]):
+        assert b >= a * (1 - 1e-12)
+
+
+def test_stationarity_at_convergence():
+    X, _ = _c1_small()
+    idx, vals = O.sample(X, 0.3, 4)
+    S = O.SampledTensor(X.shape, idx, vals, 0.3)
+    G, A = O.hooi(S, (3, 3, 3), 40)
+    for n in range(3):
+        Y = O.unfold(O.ttm_chain(S, A, skip=n), n)
+        U = O.leading_left_singular_vectors(Y, 3)
+        assert O.subspace_distance(U, A[n]) < 1e-10
+
+
+def test_reweigh_once_matches_literal_algorithm():
+    """Algorithm 2 reweighs kept entries by 1/p before HOOI; the oracle works on
+    raw values and divides the core by p.  Both give the same factors and core."""
+    X, _ = _c1_small()
+    p = 0.3
+    idx, vals = O.sample(X, p, 8)
+    raw = O.SampledTensor(X.shape, idx, vals, p)
+    literal = O.SampledTensor(X.shape, idx, vals / p, 1.0)
+    G1, A1 = O.hooi(raw, (3, 3, 3), 3)
+    G2, A2 = O.hooi(literal, (3, 3, 3), 3)
+    for a, b in zip(A1, A2):
+        assert O.subspace_distance(a, b) < 1e-12
+    A1f = [O.fix_signs(a) for a in A1]
+    A2f = [O.fix_signs(a) for a in A2]
+    np.testing.assert_allclose(O.core(raw, A1f), O.core(literal, A2f), rtol=1e-10, atol=1e-12)
+
+
+def test_hosvd_dense_and_sparse_routes_agree():
+    X, _ = _c1_small()
+    idx, vals = O.sample(X, 0.5, 2)
+    S = O.SampledTensor(X.shape, idx, vals, 0.5)
+    for k in range(3):
+        a = O.leading_left_singular_vectors(O.unfold(S.dense(), k), 3)
+        b = O.leading_eigenvectors(S.gram(k), 3)
+        assert O.subspace_distance(a, b) < 1e-10
+
+
+def test_error_decreases_towards_p_one():
+    X, Us = synth.tucker_numpy(synth.TuckerSpec((40, 30, 50), (3, 3, 3), "gaussian", 0.0, 9, "float64"))[0], None
+    errs = []
+    for p in (0.1, 0.3, 1.0):
+        S, G, A = O.mach_hooi(X, (3, 3, 3), p, 1, 2)
+        errs.append(O.relative_error(X, G, A))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-12
+
+
+def test_relative_error_slabs():
+    X, _ = _c1_small()
+    S, G, A = O.mach_hooi(X, (3, 3, 3), 0.5, 1, 1)
+    assert abs(O.relative_error(X, G, A) - O.relative_error(X, G, A, slab=7)) < 1e-13
+
+
+def test_synthetic_inverse_sum_loose():
+    """Section 4's synthetic example at the paper's size n = 200: MACH-HOOI at
+    p = 0.1 keeps the top principal component of every mode (the paper prints
+    Pearson correlations 0.9955-0.9967); checked loosely (>= 0.98)."""
+    gold = json.load(open(os.path.join(GOLDEN, "synthetic_inverse_sum.json")))
+    assert min(gold["pearson_top_pc"]) > 0.99
+    X = synth.inverse_sum_tensor(gold["n"])
+    Se = O.SampledTensor(X.shape, np.arange(X.size), X.reshape(-1), 1.0)
+    Ge, Ae = O.hooi(Se, gold["ranks"], 3)
+    S, G, A = O.mach_hooi(X, gold["ranks"], gold["p"], 2009, 3)
+    for k in range(3):
+        assert abs(O.pearson(Ae[k][:, 0], A[k][:, 0])) >= 0.98
