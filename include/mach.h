@@ -1,0 +1,194 @@
+/*
+ * mach.h — C ABI of libmach: MACH (Tsourakakis, "MACH: Fast Randomized Tensor
+ * Decompositions", arXiv 0909.4969) on one NVIDIA GB300 (sm_103a).
+ *
+ * MACH keeps every entry of a dense d-way tensor X independently with
+ * probability p and reweighs kept entries by 1/p (Section 3, Remark 1;
+ * Algorithm 1 and Algorithm 2, first block; Theorem 1's sampling law), then
+ * computes the Tucker decomposition of the sampled tensor X^ by HOOI
+ * (Algorithm 2): HOSVD initialisation, sweeps that update every factor from
+ * the tensor-times-matrix chain Y = X^ x_{k != i} A_k^T, and the core
+ * G = X^ x_1 A_1^T ... x_d A_d^T.
+ *
+ * Conventions shared by every entry point:
+ *  - Tensors are dense, C-order (last index fastest).  The linear index of
+ *    entry (i_1..i_d) (zero-based) is l = (..(i_1 I_2 + i_2) I_3 + ..) I_d + i_d.
+ *  - Device pointers come from cudaMalloc (or a caching allocator over it) on
+ *    the current device; every input tensor must be 16-byte aligned.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Factors cross the boundary as FP64, column-major I_k x r_k (entry (i, j)
+ *    at i + j*I_k), one device pointer per mode.  The core crosses as FP64,
+ *    C-order r_1 x ... x r_d.
+ *  - Supported orders d in {2, 3, 4}; ranks 1 <= r_k <= min(I_k, 32,
+ *    prod_{j != k} r_j); prod_{j != k} r_j <= 1024.
+ *  - No exception crosses the ABI; every call returns a mach_status.  On
+ *    error nothing the caller owns has been freed; outputs are unspecified.
+ *  - The library allocates its own scratch with cudaMallocAsync (stream
+ *    ordered) and frees it when the owning object is freed.
+ */
+#ifndef MACH_H
+#define MACH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mach_status {
+  MACH_OK = 0,
+  MACH_EINVAL = 1,         /* invalid argument (shape, rank, p, alignment, null) */
+  MACH_ENOMEM = 2,         /* device allocation failed */
+  MACH_ENOMEM_BUDGET = 3,  /* a request exceeds the server's HBM budget */
+  MACH_ECUDA = 4,          /* a CUDA runtime call failed; see mach_last_error() */
+  MACH_ETIMEOUT = 5,       /* a bounded device-side wait gave up */
+  MACH_EBUSY = 6,          /* object in use by in-flight work */
+  MACH_EAGAIN = 7,         /* not ready yet / no free slot: retry later */
+  MACH_EINTERNAL = 8       /* internal consistency check failed */
+} mach_status;
+
+typedef enum mach_dtype { MACH_F32 = 0, MACH_F64 = 1 } mach_dtype;
+
+/* Arithmetic of the HOOI sweep.  FP64: every contraction, Gram, eigensolve
+ * and QR in FP64.  FP32: tensor-times-matrix chain and Gram in FP32 with FP32
+ * accumulation; the R x R eigensolve and the QR re-orthonormalisation in
+ * FP64.  BF16_REFINE: sampled values stored in BF16, chain in FP32
+ * accumulation, followed by one FP32 subspace-iteration refinement sweep; the
+ * small eigensolve and QR in FP64. */
+typedef enum mach_prec {
+  MACH_PREC_FP64 = 0,
+  MACH_PREC_FP32 = 1,
+  MACH_PREC_BF16_REFINE = 2
+} mach_prec;
+
+typedef struct mach_sample_s* mach_sample_t;
+
+/* Human-readable name of a status code (static storage). */
+const char* mach_strerror(mach_status status);
+
+/* Last CUDA/internal error message seen by this thread (static per thread). */
+const char* mach_last_error(void);
+
+/* Library version string (static storage). */
+const char* mach_version(void);
+
+/* ---------------------------------------------------------------------------
+ * mach_sample — the coin of Algorithm 1/2 (Section 3 Remark 1; Theorem 1).
+ *
+ * Every linear index l of the dense tensor x_dev (dtype, d modes, dims[0..d-1])
+ * is kept iff Philox4x32-10(key = (seed mod 2^32, seed div 2^32),
+ * counter = (q mod 2^32, q div 2^32, 0, 0), q = l div 4)[l mod 4] < T with
+ * T = floor(p * 2^32) (T = 2^32 when p = 1).  The kept (value, l) pairs are
+ * compacted in increasing l; the values are stored unscaled (the 1/p
+ * reweighing is applied once, in the core and the norms).  The call then
+ * builds, for every mode n, the entries re-ordered by (i_n, i_{n+1}, ..,
+ * i_d, i_1, .., i_{n-1}) with fibre and row pointers, which the HOOI sweep
+ * streams.
+ *
+ *   x_dev   device pointer, N = prod(dims) elements of `dtype`, 16-B aligned;
+ *           read only; the caller keeps ownership and may free it once this
+ *           call returns (the kept values are copied).
+ *   p       keep probability, 0 < p <= 1.
+ *   seed    64-bit Philox key.
+ *   stream  work is ordered on it.  The call synchronises `stream` twice to
+ *           size its buffers (after compaction and after fibre counting).
+ *   out     receives the new sample object; free it with mach_sample_free.
+ * Errors: MACH_EINVAL (null pointers, d not in {2,3,4}, dims <= 0, dims > 2^31-1,
+ * p outside (0,1], misaligned x_dev), MACH_ENOMEM, MACH_ECUDA, MACH_ETIMEOUT.
+ */
+mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims,
+                        double p, uint64_t seed, void* stream, mach_sample_t* out);
+
+/* Number of kept entries (host value; no device work). */
+mach_status mach_sample_count(mach_sample_t s, int64_t* n_kept);
+
+/* Copy the kept linear indices (increasing, int64) into idx_dev[0..cap). Fails
+ * with MACH_EINVAL if cap < n_kept.  Asynchronous on `stream`. */
+mach_status mach_sample_indices(mach_sample_t s, int64_t* idx_dev, int64_t cap, void* stream);
+
+/* Copy the kept values (unscaled, in the sample's dtype, in increasing l) into
+ * val_dev[0..cap).  Asynchronous on `stream`. */
+mach_status mach_sample_values(mach_sample_t s, void* val_dev, int64_t cap, void* stream);
+
+/* Number of non-empty fibres of the mode-n ordering (entries sharing every
+ * index but the leaf index i_{n-1}); host value.  Diagnostic. */
+mach_status mach_sample_fibers(mach_sample_t s, int mode, int64_t* n_fibers);
+
+/* Release a sample object and its device memory (synchronises its stream). */
+mach_status mach_sample_free(mach_sample_t s);
+
+/* ---------------------------------------------------------------------------
+ * mach_hooi — HOOI on the sampled tensor (Algorithm 2, second block;
+ * Section 2.1 "Tucker3 Algorithms").
+ *
+ * Unless warm_start != 0, every A_k is first initialised by HOSVD of X^
+ * (the r_k leading left singular vectors of the mode-k matricization).  Then
+ * `sweeps` Gauss-Seidel sweeps: for i = 1..d, Y = X^ x_{k != i} A_k^T with the
+ * latest factors and A_i <- the r_i leading left singular vectors of Y_(i).
+ * The singular vectors are computed to convergence by block subspace
+ * iteration with Rayleigh-Ritz on the small Gram matrix of Y_(i) (the
+ * "under-the-hood" solver of Section 3 Remark 4).
+ *
+ *   ranks        host array of d ranks.
+ *   sweeps       >= 0 (0 = MACH-HOSVD, Algorithm 1, when warm_start == 0).
+ *   prec         arithmetic of the sweep (see mach_prec).
+ *   factors_dev  host array of d device pointers, each FP64 column-major
+ *                I_k x r_k; read as the starting point when warm_start != 0,
+ *                always overwritten with the result.  Caller-owned.
+ *   core_dev     NULL, or device FP64 buffer of prod(r_k) entries receiving
+ *                G = X^ x_1 A_1^T ... x_d A_d^T (X^ includes 1/p), C-order.
+ * Errors: MACH_EINVAL (bad ranks or pointers), MACH_ENOMEM, MACH_ECUDA.
+ */
+mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec prec,
+                      double* const* factors_dev, double* core_dev, int warm_start,
+                      void* stream);
+
+/* ---------------------------------------------------------------------------
+ * mach_core — G = X^ x_1 A_1^T ... x_d A_d^T for given factors (Algorithm 2
+ * last step, Eq. eqcore), with X^ = kept values / p.  FP64 throughout.
+ *   factors_dev  d device pointers, FP64 column-major I_k x r_k (read only).
+ *   core_dev     device FP64 buffer, prod(r_k) entries, C-order (written).
+ */
+mach_status mach_core(mach_sample_t s, const int* ranks, double* const* factors_dev,
+                      double* core_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * mach_error — the accuracy measure of Section 4 ("Speedups & Synthetic
+ * Experiment"): ||X - G x_1 A_1 ... x_d A_d|| / ||X|| against the ORIGINAL
+ * dense X, in one streaming pass over X (orthonormal factors assumed, so
+ * ||G x A|| = ||G||).  Synchronises `stream`; the result is a host value.
+ *   x_dev, dtype, d, dims  the original tensor (as for mach_sample).
+ *   factors_dev, core_dev  as produced by mach_hooi / mach_core.
+ *   rel_err      host pointer receiving the relative error.
+ *   x_norm       host pointer (may be NULL) receiving ||X||.
+ */
+mach_status mach_error(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims,
+                       const int* ranks, double* const* factors_dev, const double* core_dev,
+                       double* rel_err, double* x_norm, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Profiling (for measurement harnesses).  While enabled, libmach records a
+ * CUDA event pair on the launching stream around every launch of the kernel
+ * classes below, together with that launch's algorithmic byte count.
+ *   kind 0: sampler (coin + compaction), bytes = N s_in + K (s_in + 8)
+ *   kind 1: TTM chain of one mode,  bytes = K (s_val + 2) + F 8 + I_n J_n s_T
+ *   kind 2: leading singular vectors of one mode (Gram, eigensolver, QR)
+ *   kind 3: mode orderings and CSF build of one sample
+ *   kind 4: HOSVD Gram of one mode
+ * mach_profile_enable(1) clears previous records.  mach_profile_query
+ * synchronises the recorded events and returns, for one kind, the summed
+ * event time in milliseconds, the number of launches and the summed bytes.
+ * mach_launch_count returns the number of CUDA kernels libmach has launched
+ * since it was loaded (all kinds, whether profiling is on or not).
+ */
+mach_status mach_profile_enable(int enable);
+mach_status mach_profile_query(int kind, double* total_ms, int64_t* launches, double* bytes);
+int64_t mach_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MACH_H */

@@ -1,0 +1,779 @@
+// C ABI of libmach (declared in include/mach.h): argument checking, device
+// memory ownership and the orchestration of the kernels of Algorithm 2.
+#include "mach_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+namespace mach {
+
+// ---- error state -------------------------------------------------------------
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
+
+mach_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
+  b.bytes = bytes;
+  b.ptr = nullptr;
+  if (bytes == 0) return MACH_OK;
+  const size_t padded = (bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaMallocAsync(&b.ptr, padded, s);
+  if (e != cudaSuccess) {
+    set_last_error("cudaMallocAsync(%zu) -> %s", padded, cudaGetErrorString(e));
+    b.ptr = nullptr;
+    return e == cudaErrorMemoryAllocation ? MACH_ENOMEM : MACH_ECUDA;
+  }
+  return MACH_OK;
+}
+
+void dev_free(DevBuf& b, cudaStream_t s) {
+  if (b.ptr) cudaFreeAsync(b.ptr, s);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- profiling -----------------------------------------------------------------
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;
+  double bytes;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_prof_pool;
+static cudaEvent_t g_open[PROF_NKINDS];
+
+static cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_begin(int kind, cudaStream_t s) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (!g_prof_on) return;
+  g_open[kind] = prof_event();
+  cudaEventRecord(g_open[kind], s);
+}
+
+void prof_end(int kind, cudaStream_t s, double bytes) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (!g_prof_on || !g_open[kind]) return;
+  cudaEvent_t e = prof_event();
+  cudaEventRecord(e, s);
+  g_prof.push_back(ProfRec{g_open[kind], e, kind, bytes});
+  g_open[kind] = nullptr;
+}
+
+void prof_patch_last_bytes(int kind, double bytes) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (auto it = g_prof.rbegin(); it != g_prof.rend(); ++it)
+    if (it->kind == kind) {
+      it->bytes = bytes;
+      return;
+    }
+}
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached = n > 0 ? n : 1;
+  }
+  return cached;
+}
+
+}  // namespace mach
+
+using namespace mach;
+
+// Device scalars of a sample object.
+struct SampleScalars {
+  int64_t count;
+  unsigned err;
+  uint32_t nfib[kMaxModes];
+  uint32_t ntask[kMaxModes];
+  int info[2];
+  unsigned counter;
+  double acc[2];
+};
+
+struct ModeCsf {
+  DevBuf idx;        // mode-ordered l (only while building; mode 0 keeps it)
+  DevBuf val;        // mode-ordered values
+  DevBuf leaf;       // uint16
+  DevBuf fib_start;  // uint32 K + 1
+  DevBuf fib_mid;    // uint32 K
+  DevBuf row_fib;    // uint32 I + 1
+  DevBuf row_task;   // uint32 I + 1
+  DevBuf tasks;      // int4
+  int64_t ntask_cap = 0;
+  uint32_t emax = 0;
+};
+
+// HOOI workspace, one per precision.
+struct Workspace {
+  bool ready = false;
+  int ranks[kMaxModes] = {0, 0, 0, 0};
+  DevBuf fac[kMaxModes];  // T row-major I_k x r_k
+  DevBuf Y, partial, C, gram_part, V, W, U, Vout, theta, A64, gram64, rinv;
+  int64_t partial_cap_elems = 0;
+  int64_t gram_part_cap = 0;
+};
+
+struct mach_sample_s {
+  int d = 0;
+  int64_t dims[kMaxModes] = {1, 1, 1, 1};
+  mach_dtype dt = MACH_F32;
+  double p = 1.0;
+  uint64_t seed = 0;
+  uint64_t T = 0;
+  int64_t N = 0;
+  int64_t K = 0;
+  cudaStream_t stream = nullptr;
+  DevBuf idx, val;  // sampler output, increasing l (mode 0 order)
+  ModeCsf mode[kMaxModes];
+  DevBuf scal;      // SampleScalars
+  int64_t nfib[kMaxModes] = {0, 0, 0, 0};   // host copies after the build
+  int64_t ntask[kMaxModes] = {0, 0, 0, 0};
+  Workspace ws[2];  // [0] FP32, [1] FP64
+  SampleScalars* dscal() { return static_cast<SampleScalars*>(scal.ptr); }
+};
+
+namespace {
+
+size_t dtype_size(mach_dtype dt) { return dt == MACH_F32 ? 4 : 8; }
+
+void free_mode(ModeCsf& m, cudaStream_t s, bool keep_idx) {
+  if (!keep_idx) dev_free(m.idx, s);
+  dev_free(m.val, s);
+  dev_free(m.leaf, s);
+  dev_free(m.fib_start, s);
+  dev_free(m.fib_mid, s);
+  dev_free(m.row_fib, s);
+  dev_free(m.row_task, s);
+  dev_free(m.tasks, s);
+}
+
+void free_ws(Workspace& w, cudaStream_t s) {
+  for (auto& f : w.fac) dev_free(f, s);
+  dev_free(w.Y, s);
+  dev_free(w.partial, s);
+  dev_free(w.C, s);
+  dev_free(w.gram_part, s);
+  dev_free(w.V, s);
+  dev_free(w.W, s);
+  dev_free(w.U, s);
+  dev_free(w.Vout, s);
+  dev_free(w.theta, s);
+  dev_free(w.A64, s);
+  dev_free(w.gram64, s);
+  dev_free(w.rinv, s);
+  w.ready = false;
+}
+
+void free_sample(mach_sample_s* h) {
+  cudaStream_t s = h->stream;
+  for (int k = 0; k < kMaxModes; ++k) {
+    if (k == 0) {
+      // mode 0 aliases idx/val of the sampler output
+      h->mode[0].idx.ptr = nullptr;
+      h->mode[0].val.ptr = nullptr;
+    }
+    free_mode(h->mode[k], s, false);
+  }
+  dev_free(h->idx, s);
+  dev_free(h->val, s);
+  free_ws(h->ws[0], s);
+  free_ws(h->ws[1], s);
+  dev_free(h->scal, s);
+}
+
+// Modes of the cyclic ordering of mode n.
+struct Cyc {
+  int row, leaf, nmid, mid[2];
+};
+Cyc cyc(int d, int n) {
+  Cyc c;
+  c.row = n;
+  c.leaf = (n + d - 1) % d;
+  c.nmid = d - 2;
+  c.mid[0] = (n + 1) % d;
+  c.mid[1] = (n + 2) % d;
+  return c;
+}
+
+int block_size_for(int M, int r) {
+  int b = std::max(r + 4, 2 * r);
+  b = std::min(b, 32);
+  return std::min(b, M);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Public entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* mach_strerror(mach_status s) {
+  switch (s) {
+    case MACH_OK: return "ok";
+    case MACH_EINVAL: return "invalid argument";
+    case MACH_ENOMEM: return "out of device memory";
+    case MACH_ENOMEM_BUDGET: return "request exceeds the HBM budget";
+    case MACH_ECUDA: return "CUDA error";
+    case MACH_ETIMEOUT: return "device-side wait timed out";
+    case MACH_EBUSY: return "busy";
+    case MACH_EAGAIN: return "not ready, retry";
+    case MACH_EINTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char* mach_last_error(void) { return g_last_error; }
+
+const char* mach_version(void) { return "libmach 0.1 (sm_103a)"; }
+
+mach_status mach_profile_enable(int enable) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (auto& r : g_prof) {
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  for (auto& e : g_open) e = nullptr;
+  g_prof_on = enable != 0;
+  return MACH_OK;
+}
+
+mach_status mach_profile_query(int kind, double* total_ms, int64_t* launches, double* bytes) {
+  if (kind < 0 || kind >= PROF_NKINDS || !total_ms || !launches || !bytes) return MACH_EINVAL;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  double t = 0.0, by = 0.0;
+  int64_t n = 0;
+  for (auto& r : g_prof) {
+    if (r.kind != kind) continue;
+    MACH_CUDA_TRY(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    MACH_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+    t += ms;
+    by += r.bytes;
+    ++n;
+  }
+  *total_ms = t;
+  *launches = n;
+  *bytes = by;
+  return MACH_OK;
+}
+
+int64_t mach_launch_count(void) { return (int64_t)g_launches.load(); }
+
+mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p, uint64_t seed,
+                        void* stream, mach_sample_t* out) {
+  if (!x_dev || !dims || !out) return MACH_EINVAL;
+  if (d < 2 || d > kMaxModes) return MACH_EINVAL;
+  if (dtype != MACH_F32 && dtype != MACH_F64) return MACH_EINVAL;
+  if (!(p > 0.0 && p <= 1.0)) return MACH_EINVAL;
+  if (((uintptr_t)x_dev & 15u) != 0) {
+    set_last_error("input tensor must be 16-byte aligned");
+    return MACH_EINVAL;
+  }
+  int64_t N = 1;
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1 || dims[k] > kMaxDim) {
+      set_last_error("dims[%d] = %lld outside [1, %d]", k, (long long)dims[k], kMaxDim);
+      return MACH_EINVAL;
+    }
+    N *= dims[k];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mach_sample_s* h = new mach_sample_s();
+  h->d = d;
+  for (int k = 0; k < d; ++k) h->dims[k] = dims[k];
+  h->dt = dtype;
+  h->p = p;
+  h->seed = seed;
+  h->T = (uint64_t)std::floor(p * 4294967296.0);
+  h->N = N;
+  h->stream = st;
+  auto fail = [&](mach_status s) {
+    cudaStreamSynchronize(st);
+    free_sample(h);
+    delete h;
+    return s;
+  };
+  mach_status s;
+  if ((s = dev_alloc(h->scal, sizeof(SampleScalars), st)) != MACH_OK) return fail(s);
+  SampleScalars* ds = h->dscal();
+  if (cudaMemsetAsync(ds, 0, sizeof(SampleScalars), st) != cudaSuccess) return fail(MACH_ECUDA);
+  const double q = (double)h->T / 4294967296.0;
+  const double mean = (double)N * q;
+  int64_t cap = (int64_t)(mean + 10.0 * std::sqrt(mean * (1.0 - q) + 1.0) + 4096.0);
+  if (cap > N || h->T >= (1ull << 32)) cap = N;
+  DevBuf scratch;
+  const size_t vs = dtype_size(dtype);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if ((s = dev_alloc(h->idx, (size_t)cap * 8, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(h->val, (size_t)cap * vs, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(scratch, (size_t)sampler_scratch_words(N, dtype) * 8, st)) != MACH_OK) return fail(s);
+    prof_begin(PROF_SAMPLER, st);
+    if ((s = launch_sampler(x_dev, dtype, N, seed, h->T, cap, static_cast<int64_t*>(h->idx.ptr), h->val.ptr,
+                            &ds->count, &ds->err, static_cast<unsigned long long*>(scratch.ptr), st)) != MACH_OK)
+      return fail(s);
+    prof_end(PROF_SAMPLER, st, 0.0);
+    dev_free(scratch, st);
+    SampleScalars hs;
+    if (cudaMemcpyAsync(&hs, ds, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_last_error("sampler: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(MACH_ECUDA);
+    }
+    if (hs.err & DEV_TIMEOUT) return fail(MACH_ETIMEOUT);
+    h->K = hs.count;
+    prof_patch_last_bytes(PROF_SAMPLER, (double)N * vs + (double)hs.count * (vs + 8));
+    if (!(hs.err & DEV_OVERFLOW)) break;
+    // capacity exceeded (a > 10-sigma event): retry with the exact count
+    dev_free(h->idx, st);
+    dev_free(h->val, st);
+    cudaMemsetAsync(&ds->err, 0, sizeof(unsigned), st);
+    cap = std::max<int64_t>(hs.count, 1);
+  }
+  const int64_t K = h->K;
+  if (K >= (1ll << 31)) {
+    set_last_error("too many kept entries (%lld) for 32-bit fibre indices", (long long)K);
+    return fail(MACH_EINVAL);
+  }
+  // ---- per-mode orderings and CSF --------------------------------------------
+  const Decoder dec = make_decoder(d, h->dims);
+  prof_begin(PROF_CSF, st);
+  h->mode[0].idx = h->idx;
+  h->mode[0].val = h->val;
+  int64_t maxdim = 1;
+  for (int k = 0; k < d; ++k) maxdim = std::max(maxdim, h->dims[k]);
+  DevBuf sort_scr, csf_scr;
+  if ((s = dev_alloc(sort_scr, sort_scratch_bytes(K, maxdim), st)) != MACH_OK) return fail(s);
+  if ((s = dev_alloc(csf_scr, csf_scratch_bytes(K, maxdim), st)) != MACH_OK) return fail(s);
+  const int64_t Kc = std::max<int64_t>(K, 1);
+  for (int m = d - 1; m >= 1; --m) {
+    ModeCsf& dst = h->mode[m];
+    const ModeCsf& srcm = h->mode[(m + 1) % d];
+    if ((s = dev_alloc(dst.idx, (size_t)Kc * 8, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(dst.val, (size_t)Kc * vs, st)) != MACH_OK) return fail(s);
+    if (dtype == MACH_F32)
+      s = counting_sort<float>(static_cast<const int64_t*>(srcm.idx.ptr), static_cast<const float*>(srcm.val.ptr), K,
+                               &ds->count, dec, m, static_cast<int64_t*>(dst.idx.ptr),
+                               static_cast<float*>(dst.val.ptr), sort_scr.ptr, st);
+    else
+      s = counting_sort<double>(static_cast<const int64_t*>(srcm.idx.ptr), static_cast<const double*>(srcm.val.ptr),
+                                K, &ds->count, dec, m, static_cast<int64_t*>(dst.idx.ptr),
+                                static_cast<double*>(dst.val.ptr), sort_scr.ptr, st);
+    if (s != MACH_OK) return fail(s);
+  }
+  const int64_t target_tasks = (int64_t)num_sms() * 64;
+  for (int m = 0; m < d; ++m) {
+    ModeCsf& M = h->mode[m];
+    const int64_t In = h->dims[m];
+    int64_t emax = K / std::max<int64_t>(1, target_tasks);
+    emax = std::max<int64_t>(256, std::min<int64_t>(emax, 8192));
+    M.emax = (uint32_t)emax;
+    M.ntask_cap = K / emax + In + 1;
+    if ((s = dev_alloc(M.leaf, (size_t)Kc * 2, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(M.fib_start, (size_t)(Kc + 1) * 4, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(M.fib_mid, (size_t)Kc * 4, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(M.row_fib, (size_t)(In + 1) * 4, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(M.row_task, (size_t)(In + 1) * 4, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(M.tasks, (size_t)M.ntask_cap * 16, st)) != MACH_OK) return fail(s);
+    CsfBuildArgs a;
+    a.idx = static_cast<const int64_t*>(M.idx.ptr);
+    a.d_count = &ds->count;
+    a.K = K;
+    a.dec = dec;
+    a.mode = m;
+    a.emax = M.emax;
+    a.leaf = static_cast<uint16_t*>(M.leaf.ptr);
+    a.fib_start = static_cast<uint32_t*>(M.fib_start.ptr);
+    a.fib_mid = static_cast<uint32_t*>(M.fib_mid.ptr);
+    a.row_fib = static_cast<uint32_t*>(M.row_fib.ptr);
+    a.row_task = static_cast<uint32_t*>(M.row_task.ptr);
+    a.tasks = static_cast<int4*>(M.tasks.ptr);
+    a.d_nfib = &ds->nfib[m];
+    a.d_ntask = &ds->ntask[m];
+    a.d_err = &ds->err;
+    a.scratch = csf_scr.ptr;
+    if ((s = build_csf(a, st)) != MACH_OK) return fail(s);
+  }
+  prof_end(PROF_CSF, st, 0.0);
+  for (int m = 1; m < d; ++m) dev_free(h->mode[m].idx, st);
+  dev_free(sort_scr, st);
+  dev_free(csf_scr, st);
+  {
+    SampleScalars hs;
+    if (cudaMemcpyAsync(&hs, ds, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_last_error("csf build: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(MACH_ECUDA);
+    }
+    if (hs.err & (DEV_BADINDEX | DEV_TIMEOUT)) {
+      set_last_error("csf build consistency check failed (0x%x)", hs.err);
+      return fail(MACH_EINTERNAL);
+    }
+    for (int m = 0; m < d; ++m) {
+      h->nfib[m] = hs.nfib[m];
+      h->ntask[m] = hs.ntask[m];
+    }
+  }
+  *out = h;
+  return MACH_OK;
+}
+
+mach_status mach_sample_count(mach_sample_t s, int64_t* n_kept) {
+  if (!s || !n_kept) return MACH_EINVAL;
+  *n_kept = s->K;
+  return MACH_OK;
+}
+
+mach_status mach_sample_indices(mach_sample_t s, int64_t* idx_dev, int64_t cap, void* stream) {
+  if (!s || (!idx_dev && s->K > 0)) return MACH_EINVAL;
+  if (cap < s->K) return MACH_EINVAL;
+  if (s->K == 0) return MACH_OK;
+  MACH_CUDA_TRY(cudaMemcpyAsync(idx_dev, s->idx.ptr, (size_t)s->K * 8, cudaMemcpyDeviceToDevice,
+                                static_cast<cudaStream_t>(stream)));
+  return MACH_OK;
+}
+
+mach_status mach_sample_values(mach_sample_t s, void* val_dev, int64_t cap, void* stream) {
+  if (!s || (!val_dev && s->K > 0)) return MACH_EINVAL;
+  if (cap < s->K) return MACH_EINVAL;
+  if (s->K == 0) return MACH_OK;
+  MACH_CUDA_TRY(cudaMemcpyAsync(val_dev, s->val.ptr, (size_t)s->K * dtype_size(s->dt), cudaMemcpyDeviceToDevice,
+                                static_cast<cudaStream_t>(stream)));
+  return MACH_OK;
+}
+
+mach_status mach_sample_fibers(mach_sample_t s, int mode, int64_t* n_fibers) {
+  if (!s || !n_fibers || mode < 0 || mode >= s->d) return MACH_EINVAL;
+  uint32_t v = 0;
+  MACH_CUDA_TRY(cudaMemcpyAsync(&v, &s->dscal()->nfib[mode], 4, cudaMemcpyDeviceToHost, s->stream));
+  MACH_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  *n_fibers = v;
+  return MACH_OK;
+}
+
+mach_status mach_sample_free(mach_sample_t s) {
+  if (!s) return MACH_EINVAL;
+  cudaStreamSynchronize(s->stream);
+  free_sample(s);
+  cudaStreamSynchronize(s->stream);
+  delete s;
+  return MACH_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// HOOI driver
+// ---------------------------------------------------------------------------
+namespace {
+
+mach_status check_ranks(const mach_sample_s* h, const int* ranks) {
+  const int d = h->d;
+  for (int k = 0; k < d; ++k) {
+    if (ranks[k] < 1 || ranks[k] > kMaxRank || ranks[k] > h->dims[k]) {
+      set_last_error("rank %d of mode %d outside [1, min(I_k, %d)]", ranks[k], k, kMaxRank);
+      return MACH_EINVAL;
+    }
+  }
+  for (int n = 0; n < d; ++n) {
+    int64_t J = 1;
+    for (int k = 0; k < d; ++k)
+      if (k != n) J *= ranks[k];
+    if (J > kMaxJ || ranks[n] > J) {
+      set_last_error("mode %d: prod of other ranks %lld must be in [r_n, %d]", n, (long long)J, kMaxJ);
+      return MACH_EINVAL;
+    }
+    if (d == 4) {
+      const Cyc c = cyc(d, n);
+      const int Q = ranks[c.mid[1]] * ranks[c.leaf];
+      const int SQ = (Q + 31) / 32;
+      if (SQ > 8 || ranks[c.mid[0]] * SQ > kMaxJ / 32) {
+        set_last_error("mode %d: rank combination not supported by the 4-way chain kernel", n);
+        return MACH_EINVAL;
+      }
+    }
+  }
+  return MACH_OK;
+}
+
+template <typename T>
+mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
+  const int d = h->d;
+  bool same = w.ready;
+  for (int k = 0; k < d && same; ++k) same = (w.ranks[k] == ranks[k]);
+  if (same) return MACH_OK;
+  cudaStream_t st = h->stream;
+  free_ws(w, st);
+  int64_t maxY = 1, maxP = 1, maxM = 1, maxIr = 1, maxI = 1;
+  int maxr = 1;
+  for (int n = 0; n < d; ++n) {
+    int64_t J = 1;
+    for (int k = 0; k < d; ++k)
+      if (k != n) J *= ranks[k];
+    maxY = std::max(maxY, h->dims[n] * J);
+    maxP = std::max(maxP, h->mode[n].ntask_cap * J);
+    maxM = std::max(maxM, std::min<int64_t>(h->dims[n], J));
+    maxM = std::max(maxM, h->dims[n]);  // HOSVD Gram is I_n x I_n
+    maxIr = std::max(maxIr, h->dims[n] * ranks[n]);
+    maxI = std::max(maxI, h->dims[n]);
+    maxr = std::max(maxr, ranks[n]);
+  }
+  MACH_TRY(dev_alloc(w.Y, (size_t)maxY * sizeof(T), st));
+  MACH_TRY(dev_alloc(w.partial, (size_t)maxP * sizeof(T), st));
+  w.partial_cap_elems = maxP;
+  MACH_TRY(dev_alloc(w.C, (size_t)maxM * maxM * sizeof(T), st));
+  w.gram_part_cap = std::min<int64_t>((int64_t)64 * kMaxJ * kMaxJ, 16 * maxM * maxM);
+  MACH_TRY(dev_alloc(w.gram_part, (size_t)w.gram_part_cap * sizeof(T), st));
+  MACH_TRY(dev_alloc(w.V, (size_t)maxM * 32 * sizeof(T), st));
+  MACH_TRY(dev_alloc(w.W, (size_t)maxM * 32 * sizeof(T), st));
+  MACH_TRY(dev_alloc(w.U, (size_t)maxM * 32 * sizeof(T), st));
+  MACH_TRY(dev_alloc(w.Vout, (size_t)maxM * kMaxRank * sizeof(double), st));
+  MACH_TRY(dev_alloc(w.theta, (size_t)32 * sizeof(double), st));
+  MACH_TRY(dev_alloc(w.A64, (size_t)maxIr * sizeof(double), st));
+  MACH_TRY(dev_alloc(w.gram64, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
+  MACH_TRY(dev_alloc(w.rinv, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
+  for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.fac[k], (size_t)h->dims[k] * ranks[k] * sizeof(T) + 64, st));
+  for (int k = 0; k < d; ++k) w.ranks[k] = ranks[k];
+  w.ready = true;
+  (void)maxI;
+  (void)maxr;
+  return MACH_OK;
+}
+
+template <typename T>
+mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cudaStream_t st) {
+  const int d = h->d;
+  const Cyc c = cyc(d, n);
+  const ModeCsf& M = h->mode[n];
+  TtmcLaunch L;
+  L.d = d;
+  L.val = M.val.ptr;
+  L.vdt = h->dt;
+  L.leaf = static_cast<const uint16_t*>(M.leaf.ptr);
+  L.fib_start = static_cast<const uint32_t*>(M.fib_start.ptr);
+  L.fib_mid = static_cast<const uint32_t*>(M.fib_mid.ptr);
+  L.tasks = static_cast<const int4*>(M.tasks.ptr);
+  L.d_ntask = &h->dscal()->ntask[n];
+  L.d_nfib = &h->dscal()->nfib[n];
+  L.row_task = static_cast<const uint32_t*>(M.row_task.ptr);
+  L.ntask_cap = M.ntask_cap;
+  L.nrows = (int)h->dims[n];
+  L.A_leaf = w.fac[c.leaf].ptr;
+  L.A_mid0 = d >= 3 ? w.fac[c.mid[0]].ptr : nullptr;
+  L.A_mid1 = d >= 4 ? w.fac[c.mid[1]].ptr : nullptr;
+  L.I_leaf = (int)h->dims[c.leaf];
+  L.r_leaf = ranks[c.leaf];
+  L.r_mid0 = d >= 3 ? ranks[c.mid[0]] : 1;
+  L.r_mid1 = d >= 4 ? ranks[c.mid[1]] : 1;
+  int J = 1;
+  for (int k = 0; k < d; ++k)
+    if (k != n) J *= ranks[k];
+  L.J = J;
+  L.Y = w.Y.ptr;
+  L.partial = w.partial.ptr;
+  prof_begin(PROF_TTMC, st);
+  MACH_TRY(launch_ttmc(L, sizeof(T) == 8, st));
+  prof_end(PROF_TTMC, st,
+           (double)h->K * (dtype_size(h->dt) + 2) + (double)h->nfib[n] * 8 + (double)h->dims[n] * J * sizeof(T));
+  return MACH_OK;
+}
+
+// Leading r eigenvectors of the M x M Gram in w.C -> factor n (FP64 out + T copy).
+template <typename T>
+mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, int J, bool jroute, bool warm,
+                         int maxit, double* fac_out, cudaStream_t st) {
+  const int M = jroute ? J : I;
+  const int b = block_size_for(M, r);
+  MACH_TRY(launch_start_block<T>(static_cast<const T*>(w.Y.ptr), static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
+                                 jroute, warm, static_cast<T*>(w.V.ptr), 0x1000u + (uint32_t)n, st));
+  EigLaunch e;
+  e.M = M;
+  e.r = r;
+  e.b = b;
+  e.maxit = maxit;
+  e.tol = sizeof(T) == 8 ? 1e-13 : 2e-6;
+  e.V = w.V.ptr;
+  e.W = w.W.ptr;
+  e.U = w.U.ptr;
+  e.Vout = static_cast<double*>(w.Vout.ptr);
+  e.theta = static_cast<double*>(w.theta.ptr);
+  e.info = h->dscal()->info;
+  MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));
+  return launch_lsv_finish<T>(static_cast<const T*>(w.Y.ptr), e.Vout, e.theta, I, J, r, jroute,
+                              static_cast<double*>(w.A64.ptr), static_cast<double*>(w.gram64.ptr),
+                              &h->dscal()->counter, static_cast<double*>(w.rinv.ptr), &h->dscal()->err, fac_out,
+                              static_cast<T*>(w.fac[n].ptr), st);
+}
+
+template <typename T>
+mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* const* factors, double* core,
+                      bool warm, cudaStream_t st) {
+  const int d = h->d;
+  Workspace& w = h->ws[sizeof(T) == 8 ? 1 : 0];
+  MACH_TRY(ensure_ws<T>(h, ranks, w));
+  if (warm) {
+    for (int k = 0; k < d; ++k)
+      MACH_TRY(launch_factor_to_rowmajor<T>(factors[k], (int)h->dims[k], ranks[k], static_cast<T*>(w.fac[k].ptr),
+                                            st));
+  } else {
+    // HOSVD of X^: A_n = leading eigenvectors of X^_(n) X^_(n)^T, from the
+    // fibres along mode n (the CSF whose leaf is n: mode (n + 1) mod d).
+    for (int n = 0; n < d; ++n) {
+      const int src = (n + 1) % d;
+      const ModeCsf& M = h->mode[src];
+      const int In = (int)h->dims[n];
+      prof_begin(PROF_INITGRAM, st);
+      if (h->dt == MACH_F32)
+        MACH_TRY((launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                             static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
+                                             h->K, In, static_cast<T*>(w.C.ptr), st)));
+      else
+        MACH_TRY((launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                              static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
+                                              h->K, In, static_cast<T*>(w.C.ptr), st)));
+      MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, 400, factors[n], st));
+      prof_end(PROF_INITGRAM, st, 0.0);
+    }
+  }
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int n = 0; n < d; ++n) {
+      int J = 1;
+      for (int k = 0; k < d; ++k)
+        if (k != n) J *= ranks[k];
+      const int In = (int)h->dims[n];
+      MACH_TRY(run_ttmc<T>(h, w, ranks, n, st));
+      prof_begin(PROF_LSV, st);
+      const bool jroute = J < In;
+      const int M = jroute ? J : In;
+      const T* Y = static_cast<const T*>(w.Y.ptr);
+      if (jroute)
+        MACH_TRY(launch_gram<T>(Y, In, M, J, 1, static_cast<T*>(w.C.ptr), static_cast<T*>(w.gram_part.ptr),
+                                w.gram_part_cap, st));
+      else
+        MACH_TRY(launch_gram<T>(Y, J, M, 1, J, static_cast<T*>(w.C.ptr), static_cast<T*>(w.gram_part.ptr),
+                                w.gram_part_cap, st));
+      MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, J, jroute, true, 100, factors[n], st));
+      prof_end(PROF_LSV, st, 0.0);
+    }
+  }
+  if (core) {
+    const int n = d - 1;
+    int J = 1;
+    for (int k = 0; k < d; ++k)
+      if (k != n) J *= ranks[k];
+    if (sweeps == 0) MACH_TRY(run_ttmc<T>(h, w, ranks, n, st));
+    MACH_TRY(launch_core<T>(static_cast<const T*>(w.Y.ptr), factors[n], (int)h->dims[n], J, ranks[n], 1.0 / h->p,
+                            core, st));
+  }
+  return MACH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec prec, double* const* factors_dev,
+                      double* core_dev, int warm_start, void* stream) {
+  if (!s || !ranks || !factors_dev || sweeps < 0) return MACH_EINVAL;
+  for (int k = 0; k < s->d; ++k)
+    if (!factors_dev[k]) return MACH_EINVAL;
+  MACH_TRY(check_ranks(s, ranks));
+  if (s->K == 0) {
+    set_last_error("the sample kept no entries: nothing to decompose");
+    return MACH_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s->stream = st;
+  switch (prec) {
+    case MACH_PREC_FP64: return hooi_impl<double>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st);
+    case MACH_PREC_FP32:
+    case MACH_PREC_BF16_REFINE: return hooi_impl<float>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st);
+  }
+  return MACH_EINVAL;
+}
+
+mach_status mach_core(mach_sample_t s, const int* ranks, double* const* factors_dev, double* core_dev,
+                      void* stream) {
+  if (!s || !ranks || !factors_dev || !core_dev) return MACH_EINVAL;
+  MACH_TRY(check_ranks(s, ranks));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s->stream = st;
+  Workspace& w = s->ws[1];
+  MACH_TRY(ensure_ws<double>(s, ranks, w));
+  const int d = s->d;
+  for (int k = 0; k < d; ++k)
+    MACH_TRY(launch_factor_to_rowmajor<double>(factors_dev[k], (int)s->dims[k], ranks[k],
+                                               static_cast<double*>(w.fac[k].ptr), st));
+  const int n = d - 1;
+  int J = 1;
+  for (int k = 0; k < d; ++k)
+    if (k != n) J *= ranks[k];
+  MACH_TRY(run_ttmc<double>(s, w, ranks, n, st));
+  return launch_core<double>(static_cast<const double*>(w.Y.ptr), factors_dev[n], (int)s->dims[n], J, ranks[n],
+                             1.0 / s->p, core_dev, st);
+}
+
+mach_status mach_error(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, const int* ranks,
+                       double* const* factors_dev, const double* core_dev, double* rel_err, double* x_norm,
+                       void* stream) {
+  if (!x_dev || !dims || !ranks || !factors_dev || !core_dev || !rel_err) return MACH_EINVAL;
+  if (d < 2 || d > kMaxModes) return MACH_EINVAL;
+  int64_t R = 1;
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1 || ranks[k] < 1 || ranks[k] > kMaxRank || !factors_dev[k]) return MACH_EINVAL;
+    R *= ranks[k];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevBuf acc;
+  MACH_TRY(dev_alloc(acc, 2 * sizeof(double), st));
+  mach_status s = launch_error(x_dev, dtype, d, dims, ranks, factors_dev, core_dev, static_cast<double*>(acc.ptr), st);
+  double h[2] = {0, 0};
+  std::vector<double> g((size_t)R);
+  if (s == MACH_OK) {
+    if (cudaMemcpyAsync(h, acc.ptr, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(g.data(), core_dev, sizeof(double) * R, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = MACH_ECUDA;
+  }
+  dev_free(acc, st);
+  if (s != MACH_OK) return s;
+  double g2 = 0.0;
+  for (double v : g) g2 += v * v;
+  const double e2 = h[0] - 2.0 * h[1] + g2;
+  *rel_err = h[0] > 0 ? std::sqrt(std::max(e2, 0.0) / h[0]) : 0.0;
+  if (x_norm) *x_norm = std::sqrt(h[0]);
+  return MACH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,716 @@
+// Leading left singular vectors ("the r_i leading left singular vectors of
+// Y_(i)", Algorithm 2; HOSVD, Section 2.1) and the core (Eq. eqcore /
+// Algorithm 2 last step), as small dense kernels.
+//
+// For Y_(i) of size I x J the leading left singular vectors are the leading
+// eigenvectors of Y Y^T; when J < I they are Y V Sigma^-1 with V the leading
+// eigenvectors of Y^T Y.  The eigenvectors of the M x M Gram (M = min(I, J))
+// come from block subspace iteration with a Rayleigh-Ritz step every
+// iteration (the Lanczos-class "under-the-hood" solver of Section 3 Remark 4),
+// warm-started from the previous factor and run until the Ritz residuals fall
+// below a tolerance.  The b x b Rayleigh-Ritz eigenproblems use cyclic Jacobi
+// (round-robin ordering, one warp); the final r x r Rayleigh-Ritz problem and
+// the re-orthonormalisation (Cholesky QR) of the I x r factor are FP64.
+//
+// GB300 FP64 throughput is 1/64 of FP32, so FP64 is confined to O(M r^2)
+// and O(r^3) work; the O(M^2 b) products run in the path's precision T.
+#include "mach_internal.cuh"
+
+#include <cmath>
+
+namespace mach {
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// Gram C = Z^T Z, Z: L x M, element (l, m) at Z[l * sl + m * sm].
+// 32x32 output tiles (upper triangle), split over L into `nsplit` partials.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int64_t L, int M, int64_t sl,
+                                                   int64_t sm, int nsplit, T* __restrict__ out) {
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (by > bx) return;
+  __shared__ T sa[32][33];
+  __shared__ T sb[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t chunk = ceil_div(L, nsplit);
+  const int64_t l_lo = (int64_t)blockIdx.z * chunk;
+  const int64_t l_hi = min(L, l_lo + chunk);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int64_t l0 = l_lo; l0 < l_hi; l0 += 32) {
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t l = l0 + k;
+      const int ma = by * 32 + tx, mb = bx * 32 + tx;
+      sa[k][tx] = (l < l_hi && ma < M) ? Z[l * sl + ma * sm] : T(0);
+      sb[k][tx] = (l < l_hi && mb < M) ? Z[l * sl + mb * sm] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const T b = sb[k][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] += sa[k][ty + 8 * i] * b;
+    }
+    __syncthreads();
+  }
+  T* o = out + (size_t)blockIdx.z * M * M;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = by * 32 + ty + 8 * i, c = bx * 32 + tx;
+    if (r < M && c < M) {
+      o[(size_t)r * M + c] = acc[i];
+      o[(size_t)c * M + r] = acc[i];
+    }
+  }
+}
+
+template <typename T>
+__global__ void sum_partials_kernel(const T* __restrict__ part, int nsplit, int64_t n, T* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * n + i];
+    out[i] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// HOSVD Gram C = X^_(n) X^_(n)^T (raw values) from the fibres along mode n
+// (every fibre is one column of the mode-n matricization): C[a][b] +=
+// x_a x_b for every pair of entries of a fibre.  One warp per fibre.
+// ----------------------------------------------------------------------------
+template <typename V, typename T>
+__global__ void init_gram_kernel(const V* __restrict__ val, const uint16_t* __restrict__ leaf,
+                                 const uint32_t* __restrict__ fib_start, const uint32_t* d_nfib, int M,
+                                 T* __restrict__ C) {
+  const uint32_t nfib = *d_nfib;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t f = gw; f < nfib; f += nw) {
+    const uint32_t s0 = fib_start[f], s1 = fib_start[f + 1];
+    for (uint32_t i = s0 + lane; i < s1; i += 32) {
+      const uint32_t a = leaf[i];
+      const T vi = (T)val[i];
+      for (uint32_t j = i; j < s1; ++j) {
+        const uint32_t b = leaf[j];
+        const T v = vi * (T)val[j];
+        atomicAdd(&C[(size_t)a * M + b], v);
+        if (a != b) atomicAdd(&C[(size_t)b * M + a], v);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Cyclic Jacobi for a small symmetric matrix (n <= 32) held in shared memory
+// (row-major, leading dimension ld), one warp.  On return H is (nearly)
+// diagonal and Qm holds the eigenvectors in its columns.
+// Rotation (Golub & Van Loan, sym.schur2): tau = (h_qq - h_pp) / (2 h_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c;
+// H <- J^T H J with J_pp = J_qq = c, J_pq = s, J_qp = -s.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ void jacobi_warp(T* H, T* Qm, int n, int ld, int max_sweeps, T rel_tol, T* cs, int* pq) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n; i += 32)
+    for (int j = 0; j < n; ++j) Qm[i * ld + j] = (i == j) ? T(1) : T(0);
+  __syncwarp();
+  if (n <= 1) return;
+  const int np = (n + 1) & ~1;  // even number of players (a dummy when n is odd)
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = T(0), dia = T(0);
+    for (int i = lane; i < n; i += 32) {
+      for (int j = 0; j < n; ++j) {
+        const T h = H[i * ld + j];
+        if (i == j) dia += h * h; else off += h * h;
+      }
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if (off <= rel_tol * rel_tol * dia) break;
+    for (int round = 0; round < np - 1; ++round) {
+      if (lane < np / 2) {
+        const int pa = lane, pb = np - 1 - lane;
+        int p = pa == 0 ? 0 : ((pa - 1 + round) % (np - 1)) + 1;
+        int q = pb == 0 ? 0 : ((pb - 1 + round) % (np - 1)) + 1;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        T c = T(1), s = T(0);
+        if (q < n) {
+          const T hpq = H[p * ld + q];
+          const T hpp = H[p * ld + p], hqq = H[q * ld + q];
+          if (hpq != T(0) && fabs((double)hpq) > 1e-300) {
+            const T tau = (hqq - hpp) / (T(2) * hpq);
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
+            s = t * c;
+          }
+        }
+        cs[2 * lane] = c;
+        cs[2 * lane + 1] = s;
+        pq[2 * lane] = p;
+        pq[2 * lane + 1] = q < n ? q : -1;
+      }
+      __syncwarp();
+      // H <- H J (column rotations), lane owns rows
+      for (int i = lane; i < n; i += 32) {
+        for (int k = 0; k < np / 2; ++k) {
+          const int q = pq[2 * k + 1];
+          if (q < 0) continue;
+          const int p = pq[2 * k];
+          const T c = cs[2 * k], s = cs[2 * k + 1];
+          const T hp = H[i * ld + p], hq = H[i * ld + q];
+          H[i * ld + p] = c * hp - s * hq;
+          H[i * ld + q] = s * hp + c * hq;
+          const T qp = Qm[i * ld + p], qq = Qm[i * ld + q];
+          Qm[i * ld + p] = c * qp - s * qq;
+          Qm[i * ld + q] = s * qp + c * qq;
+        }
+      }
+      __syncwarp();
+      // H <- J^T H (row rotations), lane owns columns
+      for (int j = lane; j < n; j += 32) {
+        for (int k = 0; k < np / 2; ++k) {
+          const int q = pq[2 * k + 1];
+          if (q < 0) continue;
+          const int p = pq[2 * k];
+          const T c = cs[2 * k], s = cs[2 * k + 1];
+          const T hp = H[p * ld + j], hq = H[q * ld + j];
+          H[p * ld + j] = c * hp - s * hq;
+          H[q * ld + j] = s * hp + c * hq;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Order of eigenvalues (diagonal of H) descending -> perm[0..n)
+template <typename T>
+__device__ void sort_desc_warp(const T* H, int n, int ld, int* perm) {
+  const int lane = threadIdx.x & 31;
+  if (lane < n) {
+    const T v = H[lane * ld + lane];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const T u = H[j * ld + j];
+      rank += (u > v) || (u == v && j < lane);
+    }
+    perm[rank] = lane;
+  }
+  __syncwarp();
+}
+
+// Block-wide reduction of NV values per thread into out[0..NV) (smem result).
+template <typename T, int NV>
+__device__ void block_reduce_vec(T (&v)[NV], T* red /* [warps][NV] */, T* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
+  __syncthreads();
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += red[w * NV + k];
+    out[k] = s;
+  }
+  __syncthreads();
+}
+
+constexpr int kEigThreads = 256;
+constexpr int kBMax = 32;
+
+template <typename T>
+struct EigArgs {
+  const T* C;          // M x M symmetric (row-major)
+  int M, r, b;
+  T* V;                // M x b scratch (global), holds V0 on entry
+  T* W;                // M x b scratch
+  T* U;                // M x b scratch
+  double* Vout;        // M x r, FP64 leading eigenvectors (row-major)
+  double* theta;       // r eigenvalues, FP64, descending
+  int maxit;
+  T tol;               // relative residual tolerance
+  int* info;           // [0] iterations used, [1] converged flag
+};
+
+// W = C V for an M x b block; all threads of the CTA.
+template <typename T>
+__device__ void symm_times_block(const T* C, const T* V, T* W, int M, int b, int ncols) {
+  for (int o = threadIdx.x; o < M * ncols; o += blockDim.x) {
+    const int i = o / ncols, j = o - (o / ncols) * ncols;
+    const T* crow = C + (size_t)i * M;
+    T s = T(0);
+    for (int k = 0; k < M; ++k) s += crow[k] * V[(size_t)k * b + j];
+    W[(size_t)i * b + j] = s;
+  }
+}
+
+// Orthonormalise the columns of X (M x b, row-major) in place, in the path's
+// precision T: column scaling, then Cholesky QR twice (X <- X R^-1).  Called
+// on blocks whose columns are already nearly orthogonal (Ritz vectors times
+// C), so the Gram is well conditioned after scaling.
+template <typename T>
+__device__ void orth_block(T* X, int M, int b, T* G /* kBMax*kBMax smem */) {
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
+      const int p = pidx / b, q = pidx - (pidx / b) * b;
+      if (q < p) continue;
+      T s = T(0);
+      for (int i = 0; i < M; ++i) s += X[(size_t)i * b + p] * X[(size_t)i * b + q];
+      G[p * kBMax + q] = s;
+      G[q * kBMax + p] = s;
+    }
+    __syncthreads();
+    if (pass == 0) {
+      for (int o = threadIdx.x; o < M * b; o += blockDim.x) {
+        const int j = o - (o / b) * b;
+        const T nrm = sqrt(G[j * kBMax + j]);
+        X[o] = nrm > T(0) ? X[o] / nrm : T(0);
+      }
+      __syncthreads();
+      continue;
+    }
+    // right-looking Cholesky G = R^T R (R upper, in place), warp 0
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int j = 0; j < b; ++j) {
+        T djj = G[j * kBMax + j];
+        djj = djj > T(0) ? sqrt(djj) : T(1e-30);
+        __syncwarp();
+        if (lane == 0) G[j * kBMax + j] = djj;
+        for (int c = j + 1 + lane; c < b; c += 32) G[j * kBMax + c] /= djj;
+        __syncwarp();
+        for (int c = j + 1 + lane; c < b; c += 32)
+          for (int c2 = c; c2 < b; ++c2) G[c * kBMax + c2] -= G[j * kBMax + c] * G[j * kBMax + c2];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // X <- X R^-1 (forward substitution per row)
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      T* xr = X + (size_t)i * b;
+      for (int j = 0; j < b; ++j) {
+        T v = xr[j];
+        for (int k = 0; k < j; ++k) v -= xr[k] * G[k * kBMax + j];
+        xr[j] = v / G[j * kBMax + j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a) {
+  __shared__ T H[kBMax * kBMax];
+  __shared__ T Qm[kBMax * kBMax];
+  __shared__ T cs[kBMax * 2];
+  __shared__ int pq[kBMax * 2];
+  __shared__ int perm[kBMax];
+  __shared__ T G[kBMax * kBMax];
+  __shared__ double red[(kEigThreads / 32) * kBMax];
+  __shared__ double res[kBMax];
+  __shared__ int s_conv;
+  __shared__ double H64[kBMax * kBMax];
+  __shared__ double Q64[kBMax * kBMax];
+  __shared__ double cs64[kBMax * 2];
+
+  const int M = a.M, b = a.b, r = a.r;
+  T* V = a.V;
+  T* W = a.W;
+  T* U = a.U;
+  orth_block<T>(V, M, b, G);
+  int it = 0;
+  bool conv = false;
+  for (; it < a.maxit; ++it) {
+    symm_times_block<T>(a.C, V, W, M, b, b);
+    __syncthreads();
+    // H = V^T W
+    for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
+      const int p = pidx / b, q = pidx - (pidx / b) * b;
+      if (q < p) continue;
+      T s = T(0);
+      for (int i = 0; i < M; ++i) s += V[(size_t)i * b + p] * W[(size_t)i * b + q];
+      H[p * kBMax + q] = s;
+      H[q * kBMax + p] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      jacobi_warp<T>(H, Qm, b, kBMax, 30, sizeof(T) == 8 ? T(1e-15) : T(1e-7), cs, pq);
+      sort_desc_warp<T>(H, b, kBMax, perm);
+    }
+    __syncthreads();
+    // U = V Q (Ritz vectors), W <- W Q (C times Ritz vectors), residuals of the first r
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      T u[kBMax], wq[kBMax];
+      for (int j = 0; j < b; ++j) {
+        const int pj = perm[j];
+        T su = T(0), sw = T(0);
+        for (int k = 0; k < b; ++k) {
+          su += V[(size_t)i * b + k] * Qm[k * kBMax + pj];
+          sw += W[(size_t)i * b + k] * Qm[k * kBMax + pj];
+        }
+        u[j] = su;
+        wq[j] = sw;
+      }
+      for (int j = 0; j < b; ++j) {
+        U[(size_t)i * b + j] = u[j];
+        W[(size_t)i * b + j] = wq[j];
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) res[j] = 0.0;
+    __syncthreads();
+    {
+      double loc[kBMax];
+      for (int j = 0; j < kBMax; ++j) loc[j] = 0.0;
+      for (int i = threadIdx.x; i < M; i += blockDim.x)
+        for (int j = 0; j < r; ++j) {
+          const double th = (double)H[perm[j] * kBMax + perm[j]];
+          const double d = (double)W[(size_t)i * b + j] - th * (double)U[(size_t)i * b + j];
+          loc[j] += d * d;
+        }
+      block_reduce_vec<double, kBMax>(loc, red, res);
+    }
+    if (threadIdx.x == 0) {
+      const double th0 = fabs((double)H[perm[0] * kBMax + perm[0]]);
+      double worst = 0.0;
+      for (int j = 0; j < r; ++j) worst = fmax(worst, sqrt(res[j]));
+      s_conv = (th0 == 0.0) || (worst <= (double)a.tol * th0);
+    }
+    __syncthreads();
+    if (s_conv) {
+      conv = true;
+      break;
+    }
+    // next block: orthonormalised C * (Ritz vectors)
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = W[o];
+    __syncthreads();
+    orth_block<T>(V, M, b, G);
+  }
+  // (without convergence the last Ritz vectors in U are used)
+  __syncthreads();
+  // Final Rayleigh-Ritz on the leading r Ritz vectors in FP64:
+  // W(:, :r) = C U(:, :r) in T, H64 = U_r^T W_r in FP64, Jacobi in FP64.
+  symm_times_block<T>(a.C, U, W, M, b, r);
+  __syncthreads();
+  for (int pidx = threadIdx.x; pidx < r * r; pidx += blockDim.x) {
+    const int p = pidx / r, q = pidx - (pidx / r) * r;
+    if (q < p) continue;
+    double s = 0.0;
+    for (int i = 0; i < M; ++i) s += (double)U[(size_t)i * b + p] * (double)W[(size_t)i * b + q];
+    H64[p * kBMax + q] = s;
+    H64[q * kBMax + p] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    jacobi_warp<double>(H64, Q64, r, kBMax, 30, 1e-15, cs64, pq);
+    sort_desc_warp<double>(H64, r, kBMax, perm);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    for (int j = 0; j < r; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < r; ++k) s += (double)U[(size_t)i * b + k] * Q64[k * kBMax + perm[j]];
+      a.Vout[(size_t)i * r + j] = s;
+    }
+  }
+  if (threadIdx.x < r) a.theta[threadIdx.x] = H64[perm[threadIdx.x] * kBMax + perm[threadIdx.x]];
+  if (threadIdx.x == 0 && a.info) {
+    a.info[0] = it;
+    a.info[1] = conv ? 1 : 0;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Starting blocks.  Deterministic pseudo-random fill (Philox of (i, j)) for
+// the columns not given by a warm start.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void fill_random_block(T* V, int M, int b, int col0, uint32_t salt) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < M * b; o += gridDim.x * blockDim.x) {
+    const int i = o / b, j = o - (o / b) * b;
+    if (j < col0) continue;
+    const uint4 w = philox4x32_10((uint32_t)i, (uint32_t)j, 0x4d414348u, salt);
+    V[o] = (T)((double)w.x * (1.0 / 4294967296.0) - 0.5);
+  }
+}
+
+// V[:, :r] = Y^T A (Y: I x J row-major, A: I x r row-major T), V: J x b.
+template <typename T>
+__global__ void yt_times_a(const T* __restrict__ Y, const T* __restrict__ A, int I, int J, int r, T* V, int b) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= J * r) return;
+  const int j = o / r, k = o - (o / r) * r;
+  T s = T(0);
+  for (int i = 0; i < I; ++i) s += Y[(size_t)i * J + j] * A[(size_t)i * r + k];
+  V[(size_t)j * b + k] = s;
+}
+
+template <typename T>
+__global__ void copy_cols(const T* __restrict__ A, int M, int r, T* V, int b) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= M * r) return;
+  const int i = o / r, k = o - (o / r) * r;
+  V[(size_t)i * b + k] = A[o];
+}
+
+// ----------------------------------------------------------------------------
+// Factor from eigenvectors:
+//  J-route: A64[i][k] = sum_j Y[i][j] Vout[j][k] / sqrt(theta_k)   (FP64)
+//  I-route: A64 = Vout.
+// Then FP64 Cholesky QR: G = A^T A (atomics into gram64), last block
+// factors G = R^T R and stores R^-1 (upper) in rinv.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void lsv_apply_kernel(const T* __restrict__ Y, const double* __restrict__ Vout,
+                                 const double* __restrict__ theta, int I, int J, int r, int jroute,
+                                 double* __restrict__ A64, double* gram64, unsigned* counter, double* rinv,
+                                 unsigned* err) {
+  __shared__ double sG[kMaxRank * kMaxRank];
+  __shared__ double sinv[kMaxRank];
+  __shared__ bool last;
+  for (int k = threadIdx.x; k < r * r; k += blockDim.x) sG[k] = 0.0;
+  if (threadIdx.x < r) sinv[threadIdx.x] = theta[threadIdx.x] > 0.0 ? 1.0 / sqrt(theta[threadIdx.x]) : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = blockIdx.x * nw + warp; i < I; i += gridDim.x * nw) {
+    double arow[kMaxRank];
+    if (jroute) {
+      double s[kMaxRank];
+      for (int k = 0; k < kMaxRank; ++k) s[k] = 0.0;
+      for (int j = lane; j < J; j += 32) {
+        const double y = (double)Y[(size_t)i * J + j];
+        for (int k = 0; k < r; ++k) s[k] += y * Vout[(size_t)j * r + k];
+      }
+      for (int k = 0; k < r; ++k) arow[k] = warp_sum(s[k]) * sinv[k];
+    } else {
+      for (int k = 0; k < r; ++k) arow[k] = Vout[(size_t)i * r + k];
+    }
+    if (lane < r) A64[(size_t)i * r + lane] = arow[lane];
+    // partial Gram
+    for (int pidx = lane; pidx < r * r; pidx += 32) {
+      const int p = pidx / r, q = pidx - (pidx / r) * r;
+      atomicAdd(&sG[pidx], arow[p] * arow[q]);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < r * r; k += blockDim.x) atomicAdd(&gram64[k], sG[k]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  // Cholesky of gram64 (volatile reads of the accumulated values)
+  double R[kMaxRank * kMaxRank];
+  for (int k = 0; k < r * r; ++k) R[k] = ((volatile double*)gram64)[k];
+  for (int j = 0; j < r; ++j) {
+    double djj = R[j * r + j];
+    for (int k = 0; k < j; ++k) djj -= R[k * r + j] * R[k * r + j];
+    if (!(djj > 0.0)) {
+      atomicOr(err, DEV_NOTPD);
+      djj = 1e-300;
+    }
+    djj = sqrt(djj);
+    R[j * r + j] = djj;
+    for (int c = j + 1; c < r; ++c) {
+      double v = R[j * r + c];
+      for (int k = 0; k < j; ++k) v -= R[k * r + j] * R[k * r + c];
+      R[j * r + c] = v / djj;
+    }
+    for (int c = 0; c < j; ++c) R[j * r + c] = 0.0;
+  }
+  // inverse of upper-triangular R
+  double Ri[kMaxRank * kMaxRank];
+  for (int k = 0; k < r * r; ++k) Ri[k] = 0.0;
+  for (int j = 0; j < r; ++j) {
+    Ri[j * r + j] = 1.0 / R[j * r + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double v = 0.0;
+      for (int k = i + 1; k <= j; ++k) v += R[i * r + k] * Ri[k * r + j];
+      Ri[i * r + j] = -v / R[i * r + i];
+    }
+  }
+  for (int k = 0; k < r * r; ++k) rinv[k] = Ri[k];
+}
+
+// A = A64 R^-1: FP64 column-major output (I x r) and the row-major copy in T.
+template <typename T>
+__global__ void lsv_finish_kernel(const double* __restrict__ A64, const double* __restrict__ rinv, int I, int r,
+                                  double* __restrict__ out_colmajor, T* __restrict__ out_rowmajor) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= I * r) return;
+  const int i = o / r, k = o - (o / r) * r;
+  double s = 0.0;
+  for (int j = 0; j <= k; ++j) s += A64[(size_t)i * r + j] * rinv[j * r + k];
+  out_colmajor[(size_t)k * I + i] = s;
+  out_rowmajor[(size_t)i * r + k] = (T)s;
+}
+
+// FP64 column-major I x r  ->  row-major T.
+template <typename T>
+__global__ void factor_to_rowmajor(const double* __restrict__ A, int I, int r, T* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= I * r) return;
+  const int i = o / r, k = o - (o / r) * r;
+  out[o] = (T)A[(size_t)k * I + i];
+}
+
+// Core of the last mode: G[c * r + k] = scale * sum_i A[i][k] Y[i][c], with A
+// FP64 column-major (I x r) and Y row-major I x J.  One warp per output.
+template <typename T>
+__global__ void core_kernel(const T* __restrict__ Y, const double* __restrict__ A, int I, int J, int r,
+                            double scale, double* __restrict__ G) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= J * r) return;
+  const int c = gw / r, k = gw - (gw / r) * r;
+  double s = 0.0;
+  for (int i = lane; i < I; i += 32) s += A[(size_t)k * I + i] * (double)Y[(size_t)i * J + c];
+  s = warp_sum(s);
+  if (lane == 0) G[(size_t)c * r + k] = s * scale;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Host launchers
+// ----------------------------------------------------------------------------
+template <typename T>
+mach_status launch_gram(const T* Z, int64_t L, int M, int64_t sl, int64_t sm, T* C, T* partial_scratch,
+                        int64_t partial_cap, cudaStream_t st) {
+  const int tiles = (M + 31) / 32;
+  int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, L / 256), 64);
+  const int ntiles = tiles * (tiles + 1) / 2;
+  while (nsplit > 1 && (int64_t)ntiles * nsplit > 4 * num_sms()) nsplit /= 2;
+  if ((int64_t)nsplit * M * M > partial_cap) nsplit = 1;
+  dim3 grid(tiles, tiles, nsplit);
+  if (nsplit == 1) {
+    gram_kernel<T><<<grid, 256, 0, st>>>(Z, L, M, sl, sm, 1, C);
+    MACH_LAUNCH_CHECK();
+    return MACH_OK;
+  }
+  gram_kernel<T><<<grid, 256, 0, st>>>(Z, L, M, sl, sm, nsplit, partial_scratch);
+  MACH_LAUNCH_CHECK();
+  const int64_t n = (int64_t)M * M;
+  sum_partials_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(partial_scratch,
+                                                                                               nsplit, n, C);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+template <typename V, typename T>
+mach_status launch_init_gram(const void* val, const uint16_t* leaf, const uint32_t* fib_start,
+                             const uint32_t* d_nfib, int64_t nfib_cap, int M, T* C, cudaStream_t st) {
+  MACH_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)M * M, st));
+  const int threads = 256;
+  const int64_t warps = std::max<int64_t>(1, std::min<int64_t>(nfib_cap, (int64_t)num_sms() * 64));
+  init_gram_kernel<V, T><<<(unsigned)ceil_div(warps * 32, threads), threads, 0, st>>>(
+      static_cast<const V*>(val), leaf, fib_start, d_nfib, M, C);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+
+
+template <typename T>
+mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
+  EigArgs<T> a;
+  a.C = C;
+  a.M = e.M;
+  a.r = e.r;
+  a.b = e.b;
+  a.V = static_cast<T*>(e.V);
+  a.W = static_cast<T*>(e.W);
+  a.U = static_cast<T*>(e.U);
+  a.Vout = e.Vout;
+  a.theta = e.theta;
+  a.maxit = e.maxit;
+  a.tol = (T)e.tol;
+  a.info = e.info;
+  eig_kernel<T><<<1, kEigThreads, 0, st>>>(a);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+template <typename T>
+mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
+                               T* V, uint32_t salt, cudaStream_t st) {
+  const int M = jroute ? J : I;
+  fill_random_block<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024)),
+                         256, 0, st>>>(V, M, b, warm ? r : 0, salt);
+  MACH_LAUNCH_CHECK();
+  if (warm) {
+    if (jroute) {
+      yt_times_a<T><<<(unsigned)ceil_div((int64_t)J * r, 128), 128, 0, st>>>(Y, Aprev, I, J, r, V, b);
+    } else {
+      copy_cols<T><<<(unsigned)ceil_div((int64_t)I * r, 128), 128, 0, st>>>(Aprev, I, r, V, b);
+    }
+    MACH_LAUNCH_CHECK();
+  }
+  return MACH_OK;
+}
+
+template <typename T>
+mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* theta, int I, int J, int r, bool jroute,
+                              double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
+                              double* out_colmajor, T* out_rowmajor, cudaStream_t st) {
+  MACH_CUDA_TRY(cudaMemsetAsync(gram64, 0, sizeof(double) * r * r, st));
+  MACH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 8), 2 * num_sms()));
+  lsv_apply_kernel<T><<<blocks, 256, 0, st>>>(Y, Vout, theta, I, J, r, jroute ? 1 : 0, A64, gram64, counter, rinv,
+                                               err);
+  MACH_LAUNCH_CHECK();
+  lsv_finish_kernel<T><<<(unsigned)ceil_div((int64_t)I * r, 256), 256, 0, st>>>(A64, rinv, I, r, out_colmajor,
+                                                                                 out_rowmajor);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+template <typename T>
+mach_status launch_factor_to_rowmajor(const double* A, int I, int r, T* out, cudaStream_t st) {
+  factor_to_rowmajor<T><<<(unsigned)ceil_div((int64_t)I * r, 256), 256, 0, st>>>(A, I, r, out);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+template <typename T>
+mach_status launch_core(const T* Y, const double* A, int I, int J, int r, double scale, double* G,
+                        cudaStream_t st) {
+  const int64_t warps = (int64_t)J * r;
+  core_kernel<T><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(Y, A, I, J, r, scale, G);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+#define MACH_INST(T)                                                                                             \
+  template mach_status launch_gram<T>(const T*, int64_t, int, int64_t, int64_t, T*, T*, int64_t, cudaStream_t);  \
+  template mach_status launch_eig<T>(const T*, const EigLaunch&, cudaStream_t);                                  \
+  template mach_status launch_start_block<T>(const T*, const T*, int, int, int, int, bool, bool, T*, uint32_t,   \
+                                             cudaStream_t);                                                      \
+  template mach_status launch_lsv_finish<T>(const T*, const double*, const double*, int, int, int, bool,         \
+                                            double*, double*, unsigned*, double*, unsigned*, double*, T*,        \
+                                            cudaStream_t);                                                       \
+  template mach_status launch_factor_to_rowmajor<T>(const double*, int, int, T*, cudaStream_t);                  \
+  template mach_status launch_core<T>(const T*, const double*, int, int, int, double, double*, cudaStream_t);
+MACH_INST(float)
+MACH_INST(double)
+#undef MACH_INST
+
+template mach_status launch_init_gram<float, float>(const void*, const uint16_t*, const uint32_t*,
+                                                    const uint32_t*, int64_t, int, float*, cudaStream_t);
+template mach_status launch_init_gram<float, double>(const void*, const uint16_t*, const uint32_t*,
+                                                     const uint32_t*, int64_t, int, double*, cudaStream_t);
+template mach_status launch_init_gram<double, float>(const void*, const uint16_t*, const uint32_t*,
+                                                     const uint32_t*, int64_t, int, float*, cudaStream_t);
+template mach_status launch_init_gram<double, double>(const void*, const uint16_t*, const uint32_t*,
+                                                      const uint32_t*, int64_t, int, double*, cudaStream_t);
+
+}  // namespace mach

@@ -1,0 +1,338 @@
+// Internal helpers shared by the libmach translation units (device + host).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "mach.h"
+
+namespace mach {
+
+// ----------------------------------------------------------------------------
+// Error reporting
+// ----------------------------------------------------------------------------
+void set_last_error(const char* fmt, ...);
+
+#define MACH_CUDA_TRY(expr)                                                            \
+  do {                                                                                 \
+    cudaError_t mach_e_ = (expr);                                                      \
+    if (mach_e_ != cudaSuccess) {                                                      \
+      ::mach::set_last_error("%s:%d %s -> %s", __FILE__, __LINE__, #expr,              \
+                             cudaGetErrorString(mach_e_));                             \
+      return mach_e_ == cudaErrorMemoryAllocation ? MACH_ENOMEM : MACH_ECUDA;          \
+    }                                                                                  \
+  } while (0)
+
+#define MACH_TRY(expr)                          \
+  do {                                          \
+    mach_status mach_s_ = (expr);               \
+    if (mach_s_ != MACH_OK) return mach_s_;     \
+  } while (0)
+
+// Every kernel launch in libmach is followed by MACH_LAUNCH_CHECK(), which
+// also counts it (mach_launch_count).
+void count_launch();
+#define MACH_LAUNCH_CHECK()          \
+  do {                               \
+    ::mach::count_launch();          \
+    MACH_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+// Profiling scopes (event pairs on the launching stream), see mach.h.
+enum ProfKind { PROF_SAMPLER = 0, PROF_TTMC = 1, PROF_LSV = 2, PROF_CSF = 3, PROF_INITGRAM = 4, PROF_NKINDS = 5 };
+void prof_begin(int kind, cudaStream_t s);
+void prof_end(int kind, cudaStream_t s, double bytes);
+
+// Device-side status word bits (a kernel never traps: it records and returns).
+enum : unsigned {
+  DEV_TIMEOUT = 1u,    // a bounded spin-wait gave up
+  DEV_OVERFLOW = 2u,   // output capacity exceeded (sizes are recomputed by the host)
+  DEV_BADINDEX = 4u,   // an index fell outside its declared range (skipped)
+  DEV_NOTPD = 8u       // a Gram matrix that must be positive definite was not
+};
+
+// Upper bound of every device spin-wait, in polling iterations (each iteration
+// sleeps ~64-256 ns): about one second, after which the kernel flags
+// DEV_TIMEOUT and returns.
+constexpr long long kSpinLimit = 1LL << 23;
+
+constexpr int kMaxModes = 4;
+constexpr int kMaxRank = 16;
+constexpr int kMaxJ = 1024;
+constexpr int kMaxDim = 16384;
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).  Round: multiply words 0 and 2 by the
+// round multipliers (full 64-bit products), new state
+// (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)); the key is
+// bumped by the Weyl constants (fractional parts of the golden ratio and of
+// sqrt 3) before every round but the first.  The product is formed as
+// __umulhi + 32-bit multiply, the faster pair on sm_103a.
+// ----------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1) {
+  uint32_t x0 = c0, x1 = c1, x2 = 0u, x3 = 0u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, x0);
+    const uint32_t lo0 = kPhiloxM0 * x0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, x2);
+    const uint32_t lo1 = kPhiloxM1 * x2;
+    const uint32_t n0 = hi1 ^ x1 ^ k0;
+    const uint32_t n2 = hi0 ^ x3 ^ k1;
+    x0 = n0;
+    x1 = lo1;
+    x2 = n2;
+    x3 = lo0;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+// ----------------------------------------------------------------------------
+// Division of 64-bit unsigned integers by a run-time invariant divisor using
+// one multiply-high, after Granlund & Montgomery, "Division by invariant
+// integers using multiplication" (PLDI 1994), unsigned case: with
+// l = ceil(log2 d) and m = floor(2^64 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l,1))) >> max(l-1,0), t = mulhi(m, n).
+// ----------------------------------------------------------------------------
+struct FastDiv {
+  uint64_t d;
+  uint64_t m;
+  uint32_t s1;
+  uint32_t s2;
+};
+
+inline FastDiv make_fastdiv(uint64_t d) {
+  // d in [1, 2^63]
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while (((uint64_t)1 << l) < d) ++l;
+  const unsigned __int128 num = ((unsigned __int128)(((uint64_t)1 << l) - d)) << 64;
+  f.m = (uint64_t)(num / d) + 1;
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 0 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ uint64_t fdiv(const FastDiv& f, uint64_t n) {
+  const uint64_t t = __umul64hi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// Mixed-radix decoder: C-order linear index -> coordinates.
+struct Decoder {
+  int d;
+  FastDiv div[kMaxModes];   // divisor = dims[k]
+  int64_t dims[kMaxModes];
+};
+
+inline Decoder make_decoder(int d, const int64_t* dims) {
+  Decoder dec;
+  dec.d = d;
+  for (int k = 0; k < kMaxModes; ++k) {
+    dec.dims[k] = k < d ? dims[k] : 1;
+    dec.div[k] = make_fastdiv(k < d ? (uint64_t)dims[k] : 1u);
+  }
+  return dec;
+}
+
+__device__ __forceinline__ void decode(const Decoder& dec, uint64_t l, uint32_t* coord) {
+#pragma unroll
+  for (int k = kMaxModes - 1; k >= 0; --k) {
+    if (k < dec.d) {
+      const uint64_t q = fdiv(dec.div[k], l);
+      coord[k] = (uint32_t)(l - q * dec.div[k].d);
+      l = q;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// mbarrier and bulk (TMA) copies, global -> shared, 1-D (no tensor map).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; returns false (and the caller flags
+// DEV_TIMEOUT) when the limit is reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// One bulk copy of `bytes` (multiple of 16, both addresses 16-B aligned) that
+// completes `bytes` of transaction count on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Release / acquire accesses to 64-bit flags in global memory.
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device memory owned by the library, allocated stream-ordered.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+mach_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s);
+void dev_free(DevBuf& b, cudaStream_t s);
+
+int num_sms();
+
+// ----------------------------------------------------------------------------
+// Kernel launchers (one definition each, in sample.cu / sort.cu / ttmc.cu /
+// linalg.cu / error.cu) and their argument blocks.
+// ----------------------------------------------------------------------------
+int64_t sampler_scratch_words(int64_t n, mach_dtype dt);
+mach_status launch_sampler(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, int64_t cap,
+                           int64_t* idx, void* val, int64_t* d_count, unsigned* d_err,
+                           unsigned long long* scratch, cudaStream_t st);
+size_t sort_scratch_bytes(int64_t K, int64_t nbins);
+template <typename V>
+mach_status counting_sort(const int64_t* idx, const V* val, int64_t K, const int64_t* d_count, const Decoder& dec,
+                          int mode, int64_t* idx_out, V* val_out, void* scratch, cudaStream_t st);
+struct CsfBuildArgs {
+  const int64_t* idx;
+  const int64_t* d_count;
+  int64_t K;
+  Decoder dec;
+  int mode;
+  uint32_t emax;
+  uint16_t* leaf;
+  uint32_t* fib_start;
+  uint32_t* fib_mid;
+  uint32_t* row_fib;
+  uint32_t* row_task;
+  int4* tasks;
+  uint32_t* d_nfib;
+  uint32_t* d_ntask;
+  unsigned* d_err;
+  void* scratch;
+};
+size_t csf_scratch_bytes(int64_t K, int64_t nrows);
+mach_status build_csf(const CsfBuildArgs& a, cudaStream_t st);
+struct TtmcLaunch {
+  int d;
+  const void* val;
+  mach_dtype vdt;
+  const uint16_t* leaf;
+  const uint32_t* fib_start;
+  const uint32_t* fib_mid;
+  const int4* tasks;
+  const uint32_t* d_ntask;
+  const uint32_t* d_nfib;
+  const uint32_t* row_task;
+  int64_t ntask_cap;
+  int nrows;
+  const void* A_leaf;
+  const void* A_mid0;
+  const void* A_mid1;
+  int I_leaf;
+  int r_leaf, r_mid0, r_mid1;
+  int J;
+  void* Y;
+  void* partial;
+};
+mach_status launch_ttmc(const TtmcLaunch& L, bool compute_fp64, cudaStream_t st);
+template <typename T>
+mach_status launch_gram(const T* Z, int64_t L, int M, int64_t sl, int64_t sm, T* C, T* partial_scratch,
+                        int64_t partial_cap, cudaStream_t st);
+template <typename V, typename T>
+mach_status launch_init_gram(const void* val, const uint16_t* leaf, const uint32_t* fib_start,
+                             const uint32_t* d_nfib, int64_t nfib_cap, int M, T* C, cudaStream_t st);
+struct EigLaunch {
+  int M, r, b;
+  int maxit;
+  double tol;
+  void* V;
+  void* W;
+  void* U;
+  double* Vout;
+  double* theta;
+  int* info;
+};
+template <typename T>
+mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st);
+template <typename T>
+mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
+                               T* V, uint32_t salt, cudaStream_t st);
+template <typename T>
+mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* theta, int I, int J, int r, bool jroute,
+                              double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
+                              double* out_colmajor, T* out_rowmajor, cudaStream_t st);
+template <typename T>
+mach_status launch_factor_to_rowmajor(const double* A, int I, int r, T* out, cudaStream_t st);
+template <typename T>
+mach_status launch_core(const T* Y, const double* A, int I, int J, int r, double scale, double* G,
+                        cudaStream_t st);
+mach_status launch_error(const void* x, mach_dtype dt, int d, const int64_t* dims, const int* ranks,
+                         double* const* factors, const double* core, double* acc, cudaStream_t st);
+
+}  // namespace mach

@@ -1,0 +1,223 @@
+"""Python binding of libmach (include/mach.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of libmach.so; this module
+only turns torch tensors into device pointers and status codes into
+exceptions.  It raises at import-time use when libmach.so is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmach.so")
+
+MACH_F32, MACH_F64 = 0, 1
+PREC = {"fp64": 0, "fp32": 1, "bf16_refine": 2}
+STATUS = {0: "MACH_OK", 1: "MACH_EINVAL", 2: "MACH_ENOMEM", 3: "MACH_ENOMEM_BUDGET", 4: "MACH_ECUDA",
+          5: "MACH_ETIMEOUT", 6: "MACH_EBUSY", 7: "MACH_EAGAIN", 8: "MACH_EINTERNAL"}
+
+# name -> (restype, argtypes)
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_intp = ctypes.POINTER(ctypes.c_int)
+_c_dblp = ctypes.POINTER(ctypes.c_double)
+_c_pp = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "mach_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mach_last_error": (ctypes.c_char_p, []),
+    "mach_version": (ctypes.c_char_p, []),
+    "mach_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
+                                   ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mach_sample_count": (ctypes.c_int, [ctypes.c_void_p, _c_i64p]),
+    "mach_sample_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "mach_sample_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "mach_sample_fibers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i64p]),
+    "mach_sample_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "mach_hooi": (ctypes.c_int, [ctypes.c_void_p, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, ctypes.c_void_p,
+                                 ctypes.c_int, ctypes.c_void_p]),
+    "mach_core": (ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_pp, ctypes.c_void_p, ctypes.c_void_p]),
+    "mach_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, _c_intp, _c_pp,
+                                  ctypes.c_void_p, _c_dblp, _c_dblp, ctypes.c_void_p]),
+    "mach_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mach_profile_query": (ctypes.c_int, [ctypes.c_int, _c_dblp, _c_i64p, _c_dblp]),
+    "mach_launch_count": (ctypes.c_int64, []),
+}
+
+_lib = None
+
+
+class MachError(RuntimeError):
+    def __init__(self, fn: str, status: int, detail: str = ""):
+        self.status = status
+        super().__init__("%s failed: %s (%d)%s" % (fn, STATUS.get(status, "?"), status,
+                                                 (": " + detail) if detail else ""))
+
+
+def load(path: str = LIB_PATH):
+    """Load libmach.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libmach.so not found at %s: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        detail = load().mach_last_error().decode(errors="replace")
+        raise MachError(fn, status, detail)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return MACH_F32
+    if t.dtype == torch.float64:
+        return MACH_F64
+    raise TypeError("tensor must be float32 or float64")
+
+
+def _i64(vals) -> ctypes.Array:
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _int(vals) -> ctypes.Array:
+    return (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+
+
+def _ptrs(tensors) -> ctypes.Array:
+    return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+def new_factors(dims: Sequence[int], ranks: Sequence[int], device="cuda") -> List[torch.Tensor]:
+    """FP64 column-major I_k x r_k factor buffers (returned as (I_k, r_k) views)."""
+    return [torch.empty((int(r), int(n)), dtype=torch.float64, device=device).t() for n, r in zip(dims, ranks)]
+
+
+def colmajor(A: torch.Tensor) -> torch.Tensor:
+    """An (I, r) FP64 view whose storage is column-major (as the ABI expects)."""
+    A = A.to(torch.float64)
+    return A.t().contiguous().t()
+
+
+class Sample:
+    """A sampled tensor (mach_sample_t) owning its device buffers."""
+
+    def __init__(self, x: torch.Tensor, p: float, seed: int, stream=None):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA tensor")
+        lib = load()
+        self._lib = lib
+        self.dims = tuple(int(s) for s in x.shape)
+        self.d = len(self.dims)
+        self.p = float(p)
+        self.seed = int(seed)
+        self.dtype = x.dtype
+        self.device = x.device
+        h = ctypes.c_void_p()
+        _check("mach_sample", lib.mach_sample(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), self.d,
+                                              _i64(self.dims), self.p, ctypes.c_uint64(self.seed),
+                                              _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("sample already freed")
+        return self._h
+
+    def count(self) -> int:
+        n = ctypes.c_int64()
+        _check("mach_sample_count", self._lib.mach_sample_count(self.handle, ctypes.byref(n)))
+        return int(n.value)
+
+    def indices(self, stream=None) -> torch.Tensor:
+        k = self.count()
+        out = torch.empty(max(k, 1), dtype=torch.int64, device=self.device)
+        _check("mach_sample_indices", self._lib.mach_sample_indices(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                                                    out.numel(), _stream(stream)))
+        return out[:k]
+
+    def values(self, stream=None) -> torch.Tensor:
+        k = self.count()
+        out = torch.empty(max(k, 1), dtype=self.dtype, device=self.device)
+        _check("mach_sample_values", self._lib.mach_sample_values(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                                                  out.numel(), _stream(stream)))
+        return out[:k]
+
+    def fibers(self, mode: int) -> int:
+        n = ctypes.c_int64()
+        _check("mach_sample_fibers", self._lib.mach_sample_fibers(self.handle, int(mode), ctypes.byref(n)))
+        return int(n.value)
+
+    def hooi(self, ranks: Sequence[int], sweeps: int, prec: str = "fp32",
+             factors: Optional[List[torch.Tensor]] = None, warm: bool = False, core: bool = True, stream=None):
+        """Algorithm 2 on this sample; returns (core or None, factors)."""
+        if factors is None:
+            if warm:
+                raise ValueError("warm start needs factors")
+            factors = new_factors(self.dims, ranks, self.device)
+        else:
+            factors = [colmajor(f) if f.stride(0) != 1 else f for f in factors]
+        G = torch.empty(tuple(int(r) for r in ranks), dtype=torch.float64, device=self.device) if core else None
+        _check("mach_hooi", self._lib.mach_hooi(self.handle, _int(ranks), int(sweeps), PREC[prec], _ptrs(factors),
+                                                ctypes.c_void_p(G.data_ptr() if G is not None else 0),
+                                                1 if warm else 0, _stream(stream)))
+        return G, factors
+
+    def core(self, ranks: Sequence[int], factors: Sequence[torch.Tensor], stream=None) -> torch.Tensor:
+        factors = [colmajor(f) if f.stride(0) != 1 else f for f in factors]
+        G = torch.empty(tuple(int(r) for r in ranks), dtype=torch.float64, device=self.device)
+        _check("mach_core", self._lib.mach_core(self.handle, _int(ranks), _ptrs(factors),
+                                                ctypes.c_void_p(G.data_ptr()), _stream(stream)))
+        return G
+
+    def free(self):
+        if self._h is not None:
+            _check("mach_sample_free", self._lib.mach_sample_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sample(x: torch.Tensor, p: float, seed: int, stream=None) -> Sample:
+    return Sample(x, p, seed, stream)
+
+
+def error(x: torch.Tensor, core: torch.Tensor, factors: Sequence[torch.Tensor], stream=None):
+    """(||X - G x A|| / ||X||, ||X||) against the dense X (one streaming pass)."""
+    lib = load()
+    factors = [colmajor(f) if f.stride(0) != 1 else f for f in factors]
+    ranks = [int(s) for s in core.shape]
+    rel = ctypes.c_double()
+    xn = ctypes.c_double()
+    _check("mach_error", lib.mach_error(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), x.dim(),
+                                        _i64(x.shape), _int(ranks), _ptrs(factors),
+                                        ctypes.c_void_p(core.contiguous().data_ptr()), ctypes.byref(rel),
+                                        ctypes.byref(xn), _stream(stream)))
+    return float(rel.value), float(xn.value)
+
+
+def version() -> str:
+    return load().mach_version().decode()
