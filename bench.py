@@ -248,9 +248,13 @@ def main():
     if N * X.element_size() <= 256 * 2 ** 20:
         flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
+    last_stats = {}
+
     def step(x):
         s = mach.sample(x, w.p, spec_r.seed)
         G, A = s.hooi(ranks, w.sweeps, prec)
+        last_stats.clear()
+        last_stats.update(s.stats())
         s.free()
         return G, A
 
@@ -363,7 +367,8 @@ def main():
                 "p99_ms": sorted(per_step)[max(0, math.ceil(0.99 * len(per_step)) - 1)],
                 "sampler_gbs": samp_gbs, "sampler_frac_of_hbm": samp_gbs / hbm_peak,
                 "roofline": roofline, "profile_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+                "eigensolver": last_stats}
         print(json.dumps(line))
     if world > 1:
         dist.barrier()

@@ -20,8 +20,9 @@
  *  - Factors cross the boundary as FP64, column-major I_k x r_k (entry (i, j)
  *    at i + j*I_k), one device pointer per mode.  The core crosses as FP64,
  *    C-order r_1 x ... x r_d.
- *  - Supported orders d in {2, 3, 4}; ranks 1 <= r_k <= min(I_k, 32,
- *    prod_{j != k} r_j); prod_{j != k} r_j <= 1024.
+ *  - Supported orders d in {2, 3, 4}; dims 1 <= I_k <= 16384; ranks
+ *    1 <= r_k <= min(I_k, 16, prod_{j != k} r_j); prod_{j != k} r_j <= 1024;
+ *    fewer than 2^31 kept entries.
  *  - No exception crosses the ABI; every call returns a mach_status.  On
  *    error nothing the caller owns has been freed; outputs are unspecified.
  *  - The library allocates its own scratch with cudaMallocAsync (stream
@@ -92,11 +93,13 @@ const char* mach_version(void);
  *           call returns (the kept values are copied).
  *   p       keep probability, 0 < p <= 1.
  *   seed    64-bit Philox key.
- *   stream  work is ordered on it.  The call synchronises `stream` twice to
- *           size its buffers (after compaction and after fibre counting).
+ *   stream  work is ordered on it.  The call synchronises `stream` twice:
+ *           after compaction (to size its buffers) and at the end (fibre
+ *           counts and consistency checks).
  *   out     receives the new sample object; free it with mach_sample_free.
- * Errors: MACH_EINVAL (null pointers, d not in {2,3,4}, dims <= 0, dims > 2^31-1,
- * p outside (0,1], misaligned x_dev), MACH_ENOMEM, MACH_ECUDA, MACH_ETIMEOUT.
+ * Errors: MACH_EINVAL (null pointers, d not in {2,3,4}, dims outside
+ * [1, 16384], p outside (0,1], misaligned x_dev, 2^31 or more kept entries),
+ * MACH_ENOMEM, MACH_ECUDA, MACH_ETIMEOUT, MACH_EINTERNAL (ordering check).
  */
 mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims,
                         double p, uint64_t seed, void* stream, mach_sample_t* out);
@@ -115,6 +118,15 @@ mach_status mach_sample_values(mach_sample_t s, void* val_dev, int64_t cap, void
 /* Number of non-empty fibres of the mode-n ordering (entries sharing every
  * index but the leaf index i_{n-1}); host value.  Diagnostic. */
 mach_status mach_sample_fibers(mach_sample_t s, int mode, int64_t* n_fibers);
+
+/* Diagnostics accumulated over every mach_hooi / mach_core call on this
+ * sample (synchronises its stream): number of leading-singular-vector solves,
+ * their total subspace iterations, how many stopped at the iteration cap
+ * before reaching the tolerance, and the device status bits (timeouts,
+ * overflow, index and positive-definiteness checks; 0 = clean).  Any pointer
+ * may be NULL. */
+mach_status mach_sample_stats(mach_sample_t s, int64_t* eig_calls, int64_t* eig_iters,
+                              int64_t* eig_unconverged, unsigned* device_flags);
 
 /* Release a sample object and its device memory (synchronises its stream). */
 mach_status mach_sample_free(mach_sample_t s);

@@ -26,7 +26,9 @@ mach_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
   b.bytes = bytes;
   b.ptr = nullptr;
   if (bytes == 0) return MACH_OK;
-  const size_t padded = (bytes + 255) & ~(size_t)255;
+  // 256 bytes of slack past the end: 16-byte-granular bulk copies may round a
+  // range end up by up to 15 bytes (never used, never written).
+  const size_t padded = ((bytes + 255) & ~(size_t)255) + 256;
   cudaError_t e = cudaMallocAsync(&b.ptr, padded, s);
   if (e != cudaSuccess) {
     set_last_error("cudaMallocAsync(%zu) -> %s", padded, cudaGetErrorString(e));
@@ -115,7 +117,8 @@ struct SampleScalars {
   unsigned err;
   uint32_t nfib[kMaxModes];
   uint32_t ntask[kMaxModes];
-  int info[2];
+  unsigned long long eig_stats[3];   // eigensolver calls, iterations, unconverged
+  unsigned long long eig_ctl[8];     // split-path iteration control
   unsigned counter;
   double acc[2];
 };
@@ -397,7 +400,7 @@ mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_
     ModeCsf& M = h->mode[m];
     const int64_t In = h->dims[m];
     int64_t emax = K / std::max<int64_t>(1, target_tasks);
-    emax = std::max<int64_t>(256, std::min<int64_t>(emax, 8192));
+    emax = std::max<int64_t>(256, std::min<int64_t>(emax, (int64_t)ttmc_task_max()));
     M.emax = (uint32_t)emax;
     M.ntask_cap = K / emax + In + 1;
     if ((s = dev_alloc(M.leaf, (size_t)Kc * 2, st)) != MACH_OK) return fail(s);
@@ -479,6 +482,19 @@ mach_status mach_sample_fibers(mach_sample_t s, int mode, int64_t* n_fibers) {
   MACH_CUDA_TRY(cudaMemcpyAsync(&v, &s->dscal()->nfib[mode], 4, cudaMemcpyDeviceToHost, s->stream));
   MACH_CUDA_TRY(cudaStreamSynchronize(s->stream));
   *n_fibers = v;
+  return MACH_OK;
+}
+
+mach_status mach_sample_stats(mach_sample_t s, int64_t* eig_calls, int64_t* eig_iters, int64_t* eig_unconverged,
+                              unsigned* device_flags) {
+  if (!s) return MACH_EINVAL;
+  SampleScalars hs;
+  MACH_CUDA_TRY(cudaMemcpyAsync(&hs, s->dscal(), sizeof(hs), cudaMemcpyDeviceToHost, s->stream));
+  MACH_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (eig_calls) *eig_calls = (int64_t)hs.eig_stats[0];
+  if (eig_iters) *eig_iters = (int64_t)hs.eig_stats[1];
+  if (eig_unconverged) *eig_unconverged = (int64_t)hs.eig_stats[2];
+  if (device_flags) *device_flags = hs.err;
   return MACH_OK;
 }
 
@@ -602,6 +618,7 @@ mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cu
   L.J = J;
   L.Y = w.Y.ptr;
   L.partial = w.partial.ptr;
+  L.err = &h->dscal()->err;
   prof_begin(PROF_TTMC, st);
   MACH_TRY(launch_ttmc(L, sizeof(T) == 8, st));
   prof_end(PROF_TTMC, st,
@@ -628,7 +645,8 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.U = w.U.ptr;
   e.Vout = static_cast<double*>(w.Vout.ptr);
   e.theta = static_cast<double*>(w.theta.ptr);
-  e.info = h->dscal()->info;
+  e.ctl = h->dscal()->eig_ctl;
+  e.stats = h->dscal()->eig_stats;
   MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));
   return launch_lsv_finish<T>(static_cast<const T*>(w.Y.ptr), e.Vout, e.theta, I, J, r, jroute,
                               static_cast<double*>(w.A64.ptr), static_cast<double*>(w.gram64.ptr),
@@ -662,7 +680,10 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
         MACH_TRY((launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
                                               static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
                                               h->K, In, static_cast<T*>(w.C.ptr), st)));
-      MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, 400, factors[n], st));
+      // With sweeps to follow, HOOI refines the start, so the HOSVD Gram's
+      // eigenvectors are iterated at most 40 times; MACH-HOSVD alone (no
+      // sweeps) iterates to convergence (at most 400).
+      MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, sweeps > 0 ? 40 : 400, factors[n], st));
       prof_end(PROF_INITGRAM, st, 0.0);
     }
   }

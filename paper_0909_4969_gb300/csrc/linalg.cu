@@ -225,22 +225,45 @@ __device__ void block_reduce_vec(T (&v)[NV], T* red /* [warps][NV] */, T* out) {
 
 constexpr int kEigThreads = 256;
 constexpr int kBMax = 32;
+constexpr int kEigSmallMax = 256;   // larger Grams take the split (multi-CTA) path
+
+// Shared-memory state of one Rayleigh-Ritz step.
+template <typename T>
+struct RRShared {
+  T H[kBMax * kBMax];
+  T Qm[kBMax * kBMax];
+  T G[kBMax * kBMax];
+  T cs[kBMax * 2];
+  int pq[kBMax * 2];
+  int perm[kBMax];
+  double red[(kEigThreads / 32) * kBMax];
+  double res[kBMax];
+  int conv;
+};
+
+// Iteration control kept in global memory between split-path launches.
+struct EigCtl {
+  int done;
+  int it;
+  double prev_worst;
+};
 
 template <typename T>
 struct EigArgs {
   const T* C;          // M x M symmetric (row-major)
   int M, r, b;
-  T* V;                // M x b scratch (global), holds V0 on entry
-  T* W;                // M x b scratch
-  T* U;                // M x b scratch
+  T* V;                // M x b, holds V0 on entry
+  T* W;                // M x b
+  T* U;                // M x b
   double* Vout;        // M x r, FP64 leading eigenvectors (row-major)
   double* theta;       // r eigenvalues, FP64, descending
   int maxit;
-  T tol;               // relative residual tolerance
-  int* info;           // [0] iterations used, [1] converged flag
+  double tol;          // relative residual tolerance
+  EigCtl* ctl;         // split path only
+  unsigned long long* stats;  // [0] calls, [1] iterations, [2] unconverged
 };
 
-// W = C V for an M x b block; all threads of the CTA.
+// W[:, :ncols] = C V[:, :ncols] for an M x b block; all threads of the CTA.
 template <typename T>
 __device__ void symm_times_block(const T* C, const T* V, T* W, int M, int b, int ncols) {
   for (int o = threadIdx.x; o < M * ncols; o += blockDim.x) {
@@ -253,11 +276,11 @@ __device__ void symm_times_block(const T* C, const T* V, T* W, int M, int b, int
 }
 
 // Orthonormalise the columns of X (M x b, row-major) in place, in the path's
-// precision T: column scaling, then Cholesky QR twice (X <- X R^-1).  Called
-// on blocks whose columns are already nearly orthogonal (Ritz vectors times
-// C), so the Gram is well conditioned after scaling.
+// precision T: column scaling, then Cholesky QR twice (X <- X R^-1).  Used on
+// blocks whose columns are already nearly orthogonal (C times Ritz vectors),
+// so the Gram is well conditioned after scaling.
 template <typename T>
-__device__ void orth_block(T* X, int M, int b, T* G /* kBMax*kBMax smem */) {
+__device__ void orth_block(T* X, int M, int b, T* G) {
   for (int pass = 0; pass < 3; ++pass) {
     for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
       const int p = pidx / b, q = pidx - (pidx / b) * b;
@@ -293,7 +316,6 @@ __device__ void orth_block(T* X, int M, int b, T* G /* kBMax*kBMax smem */) {
       }
     }
     __syncthreads();
-    // X <- X R^-1 (forward substitution per row)
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       T* xr = X + (size_t)i * b;
       for (int j = 0; j < b; ++j) {
@@ -306,100 +328,80 @@ __device__ void orth_block(T* X, int M, int b, T* G /* kBMax*kBMax smem */) {
   }
 }
 
+// One Rayleigh-Ritz step given V (orthonormal, M x b) and W = C V:
+// H = V^T W, H = Q Theta Q^T (Jacobi), U = V Q (Ritz vectors), W <- W Q,
+// residuals ||W_j - theta_j U_j|| of the leading r.  Converged when every
+// residual is below tol * theta_1, or when the residual has reached the
+// arithmetic's floor (below 100 tol and no longer halving).  If not
+// converged, V <- orth(W) for the next power step.  Returns converged.
 template <typename T>
-__global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a) {
-  __shared__ T H[kBMax * kBMax];
-  __shared__ T Qm[kBMax * kBMax];
-  __shared__ T cs[kBMax * 2];
-  __shared__ int pq[kBMax * 2];
-  __shared__ int perm[kBMax];
-  __shared__ T G[kBMax * kBMax];
-  __shared__ double red[(kEigThreads / 32) * kBMax];
-  __shared__ double res[kBMax];
-  __shared__ int s_conv;
-  __shared__ double H64[kBMax * kBMax];
-  __shared__ double Q64[kBMax * kBMax];
-  __shared__ double cs64[kBMax * 2];
-
-  const int M = a.M, b = a.b, r = a.r;
-  T* V = a.V;
-  T* W = a.W;
-  T* U = a.U;
-  orth_block<T>(V, M, b, G);
-  int it = 0;
-  bool conv = false;
-  for (; it < a.maxit; ++it) {
-    symm_times_block<T>(a.C, V, W, M, b, b);
-    __syncthreads();
-    // H = V^T W
-    for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
-      const int p = pidx / b, q = pidx - (pidx / b) * b;
-      if (q < p) continue;
-      T s = T(0);
-      for (int i = 0; i < M; ++i) s += V[(size_t)i * b + p] * W[(size_t)i * b + q];
-      H[p * kBMax + q] = s;
-      H[q * kBMax + p] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      jacobi_warp<T>(H, Qm, b, kBMax, 30, sizeof(T) == 8 ? T(1e-15) : T(1e-7), cs, pq);
-      sort_desc_warp<T>(H, b, kBMax, perm);
-    }
-    __syncthreads();
-    // U = V Q (Ritz vectors), W <- W Q (C times Ritz vectors), residuals of the first r
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-      T u[kBMax], wq[kBMax];
-      for (int j = 0; j < b; ++j) {
-        const int pj = perm[j];
-        T su = T(0), sw = T(0);
-        for (int k = 0; k < b; ++k) {
-          su += V[(size_t)i * b + k] * Qm[k * kBMax + pj];
-          sw += W[(size_t)i * b + k] * Qm[k * kBMax + pj];
-        }
-        u[j] = su;
-        wq[j] = sw;
-      }
-      for (int j = 0; j < b; ++j) {
-        U[(size_t)i * b + j] = u[j];
-        W[(size_t)i * b + j] = wq[j];
-      }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < r; j += blockDim.x) res[j] = 0.0;
-    __syncthreads();
-    {
-      double loc[kBMax];
-      for (int j = 0; j < kBMax; ++j) loc[j] = 0.0;
-      for (int i = threadIdx.x; i < M; i += blockDim.x)
-        for (int j = 0; j < r; ++j) {
-          const double th = (double)H[perm[j] * kBMax + perm[j]];
-          const double d = (double)W[(size_t)i * b + j] - th * (double)U[(size_t)i * b + j];
-          loc[j] += d * d;
-        }
-      block_reduce_vec<double, kBMax>(loc, red, res);
-    }
-    if (threadIdx.x == 0) {
-      const double th0 = fabs((double)H[perm[0] * kBMax + perm[0]]);
-      double worst = 0.0;
-      for (int j = 0; j < r; ++j) worst = fmax(worst, sqrt(res[j]));
-      s_conv = (th0 == 0.0) || (worst <= (double)a.tol * th0);
-    }
-    __syncthreads();
-    if (s_conv) {
-      conv = true;
-      break;
-    }
-    // next block: orthonormalised C * (Ritz vectors)
-    for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = W[o];
-    __syncthreads();
-    orth_block<T>(V, M, b, G);
+__device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, double* prev_worst, RRShared<T>& sh) {
+  for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
+    const int p = pidx / b, q = pidx - (pidx / b) * b;
+    if (q < p) continue;
+    T s = T(0);
+    for (int i = 0; i < M; ++i) s += V[(size_t)i * b + p] * W[(size_t)i * b + q];
+    sh.H[p * kBMax + q] = s;
+    sh.H[q * kBMax + p] = s;
   }
-  // (without convergence the last Ritz vectors in U are used)
   __syncthreads();
-  // Final Rayleigh-Ritz on the leading r Ritz vectors in FP64:
-  // W(:, :r) = C U(:, :r) in T, H64 = U_r^T W_r in FP64, Jacobi in FP64.
-  symm_times_block<T>(a.C, U, W, M, b, r);
+  if (threadIdx.x < 32) {
+    jacobi_warp<T>(sh.H, sh.Qm, b, kBMax, 30, sizeof(T) == 8 ? T(1e-15) : T(1e-7), sh.cs, sh.pq);
+    sort_desc_warp<T>(sh.H, b, kBMax, sh.perm);
+  }
   __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    T u[kBMax], wq[kBMax];
+    for (int j = 0; j < b; ++j) {
+      const int pj = sh.perm[j];
+      T su = T(0), sw = T(0);
+      for (int k = 0; k < b; ++k) {
+        su += V[(size_t)i * b + k] * sh.Qm[k * kBMax + pj];
+        sw += W[(size_t)i * b + k] * sh.Qm[k * kBMax + pj];
+      }
+      u[j] = su;
+      wq[j] = sw;
+    }
+    for (int j = 0; j < b; ++j) {
+      U[(size_t)i * b + j] = u[j];
+      W[(size_t)i * b + j] = wq[j];
+    }
+  }
+  __syncthreads();
+  {
+    double loc[kBMax];
+    for (int j = 0; j < kBMax; ++j) loc[j] = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x)
+      for (int j = 0; j < r; ++j) {
+        const double th = (double)sh.H[sh.perm[j] * kBMax + sh.perm[j]];
+        const double d = (double)W[(size_t)i * b + j] - th * (double)U[(size_t)i * b + j];
+        loc[j] += d * d;
+      }
+    block_reduce_vec<double, kBMax>(loc, sh.red, sh.res);
+  }
+  if (threadIdx.x == 0) {
+    const double th0 = fabs((double)sh.H[sh.perm[0] * kBMax + sh.perm[0]]);
+    double worst = 0.0;
+    for (int j = 0; j < r; ++j) worst = fmax(worst, sqrt(sh.res[j]));
+    const double rel = th0 > 0.0 ? worst / th0 : 0.0;
+    const bool floor_hit = rel < 100.0 * tol && rel > 0.5 * (*prev_worst);
+    sh.conv = (th0 == 0.0) || (rel <= tol) || floor_hit;
+    *prev_worst = rel;
+  }
+  __syncthreads();
+  if (sh.conv) return true;
+  for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = W[o];
+  __syncthreads();
+  orth_block<T>(V, M, b, sh.G);
+  return false;
+}
+
+// Final Rayleigh-Ritz of the leading r Ritz vectors in FP64: with
+// W[:, :r] = C U[:, :r], H64 = U_r^T W_r (FP64 accumulation), FP64 Jacobi,
+// Vout = U_r Q64 (FP64).
+template <typename T>
+__device__ void final_rr(const T* U, const T* W, int M, int b, int r, double* Vout, double* theta,
+                         RRShared<T>& sh, double* H64, double* Q64, double* cs64) {
   for (int pidx = threadIdx.x; pidx < r * r; pidx += blockDim.x) {
     const int p = pidx / r, q = pidx - (pidx / r) * r;
     if (q < p) continue;
@@ -410,21 +412,122 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a) {
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    jacobi_warp<double>(H64, Q64, r, kBMax, 30, 1e-15, cs64, pq);
-    sort_desc_warp<double>(H64, r, kBMax, perm);
+    jacobi_warp<double>(H64, Q64, r, kBMax, 30, 1e-15, cs64, sh.pq);
+    sort_desc_warp<double>(H64, r, kBMax, sh.perm);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     for (int j = 0; j < r; ++j) {
       double s = 0.0;
-      for (int k = 0; k < r; ++k) s += (double)U[(size_t)i * b + k] * Q64[k * kBMax + perm[j]];
-      a.Vout[(size_t)i * r + j] = s;
+      for (int k = 0; k < r; ++k) s += (double)U[(size_t)i * b + k] * Q64[k * kBMax + sh.perm[j]];
+      Vout[(size_t)i * r + j] = s;
     }
   }
-  if (threadIdx.x < r) a.theta[threadIdx.x] = H64[perm[threadIdx.x] * kBMax + perm[threadIdx.x]];
-  if (threadIdx.x == 0 && a.info) {
-    a.info[0] = it;
-    a.info[1] = conv ? 1 : 0;
+  if (threadIdx.x < r) theta[threadIdx.x] = H64[sh.perm[threadIdx.x] * kBMax + sh.perm[threadIdx.x]];
+  __syncthreads();
+}
+
+// Fused path (one CTA, small M): orth, iterate power step + Rayleigh-Ritz,
+// final FP64 Rayleigh-Ritz.
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a) {
+  __shared__ RRShared<T> sh;
+  __shared__ double H64[kBMax * kBMax];
+  __shared__ double Q64[kBMax * kBMax];
+  __shared__ double cs64[kBMax * 2];
+  __shared__ double prev;
+  const int M = a.M, b = a.b, r = a.r;
+  if (threadIdx.x == 0) prev = 1e300;
+  orth_block<T>(a.V, M, b, sh.G);
+  int it = 0;
+  bool conv = false;
+  for (; it < a.maxit; ++it) {
+    symm_times_block<T>(a.C, a.V, a.W, M, b, b);
+    __syncthreads();
+    if (rr_step<T>(a.V, a.W, a.U, M, b, r, a.tol, &prev, sh)) {
+      conv = true;
+      break;
+    }
+  }
+  symm_times_block<T>(a.C, a.U, a.W, M, b, r);
+  __syncthreads();
+  final_rr<T>(a.U, a.W, M, b, r, a.Vout, a.theta, sh, H64, Q64, cs64);
+  if (threadIdx.x == 0 && a.stats) {
+    atomicAdd(&a.stats[0], 1ull);
+    atomicAdd(&a.stats[1], (unsigned long long)(it + (conv ? 1 : 0)));
+    if (!conv) atomicAdd(&a.stats[2], 1ull);
+  }
+}
+
+// Split path (large M): eig_begin (orth), then per iteration the multi-CTA
+// product and the single-CTA Rayleigh-Ritz step, then the product with the
+// leading Ritz vectors and eig_end (FP64 Rayleigh-Ritz).  Iterations after
+// convergence return at once (device flag).
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) eig_begin_kernel(EigArgs<T> a) {
+  __shared__ RRShared<T> sh;
+  if (threadIdx.x == 0) {
+    a.ctl->done = 0;
+    a.ctl->it = 0;
+    a.ctl->prev_worst = 1e300;
+  }
+  orth_block<T>(a.V, a.M, a.b, sh.G);
+}
+
+// W[:, :ncols] = C V[:, :ncols]; one warp per row of C, lanes over columns of
+// C (coalesced), b partial sums per lane reduced by shuffles.
+template <typename T>
+__global__ void __launch_bounds__(256) symm_mul_kernel(EigArgs<T> a, const T* V, T* W, int ncols, int respect_done) {
+  if (respect_done && a.ctl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= a.M) return;
+  const T* crow = a.C + (size_t)row * a.M;
+  T s[kBMax];
+#pragma unroll
+  for (int j = 0; j < kBMax; ++j) s[j] = T(0);
+  for (int k = lane; k < a.M; k += 32) {
+    const T c = crow[k];
+    const T* vr = V + (size_t)k * a.b;
+#pragma unroll
+    for (int j = 0; j < kBMax; ++j)
+      if (j < ncols) s[j] += c * vr[j];
+  }
+#pragma unroll
+  for (int j = 0; j < kBMax; ++j) {
+    if (j < ncols) {
+      const T v = warp_sum(s[j]);
+      if (lane == 0) W[(size_t)row * a.b + j] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) eig_step_kernel(EigArgs<T> a) {
+  __shared__ RRShared<T> sh;
+  __shared__ double prev;
+  if (a.ctl->done) return;
+  if (threadIdx.x == 0) prev = a.ctl->prev_worst;
+  __syncthreads();
+  const bool conv = rr_step<T>(a.V, a.W, a.U, a.M, a.b, a.r, a.tol, &prev, sh);
+  if (threadIdx.x == 0) {
+    a.ctl->it += 1;
+    a.ctl->prev_worst = prev;
+    if (conv || a.ctl->it >= a.maxit) a.ctl->done = conv ? 1 : 2;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) eig_end_kernel(EigArgs<T> a) {
+  __shared__ RRShared<T> sh;
+  __shared__ double H64[kBMax * kBMax];
+  __shared__ double Q64[kBMax * kBMax];
+  __shared__ double cs64[kBMax * 2];
+  final_rr<T>(a.U, a.W, a.M, a.b, a.r, a.Vout, a.theta, sh, H64, Q64, cs64);
+  if (threadIdx.x == 0 && a.stats) {
+    atomicAdd(&a.stats[0], 1ull);
+    atomicAdd(&a.stats[1], (unsigned long long)a.ctl->it);
+    if (a.ctl->done != 1) atomicAdd(&a.stats[2], 1ull);
   }
 }
 
@@ -633,9 +736,26 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
   a.Vout = e.Vout;
   a.theta = e.theta;
   a.maxit = e.maxit;
-  a.tol = (T)e.tol;
-  a.info = e.info;
-  eig_kernel<T><<<1, kEigThreads, 0, st>>>(a);
+  a.tol = e.tol;
+  a.ctl = static_cast<EigCtl*>(e.ctl);
+  a.stats = e.stats;
+  if (e.M <= kEigSmallMax) {
+    eig_kernel<T><<<1, kEigThreads, 0, st>>>(a);
+    MACH_LAUNCH_CHECK();
+    return MACH_OK;
+  }
+  const unsigned rows = (unsigned)ceil_div(e.M, 8);
+  eig_begin_kernel<T><<<1, kEigThreads, 0, st>>>(a);
+  MACH_LAUNCH_CHECK();
+  for (int it = 0; it < e.maxit; ++it) {
+    symm_mul_kernel<T><<<rows, 256, 0, st>>>(a, a.V, a.W, e.b, 1);
+    MACH_LAUNCH_CHECK();
+    eig_step_kernel<T><<<1, kEigThreads, 0, st>>>(a);
+    MACH_LAUNCH_CHECK();
+  }
+  symm_mul_kernel<T><<<rows, 256, 0, st>>>(a, a.U, a.W, e.r, 0);
+  MACH_LAUNCH_CHECK();
+  eig_end_kernel<T><<<1, kEigThreads, 0, st>>>(a);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }

@@ -299,7 +299,9 @@ struct TtmcLaunch {
   int J;
   void* Y;
   void* partial;
+  unsigned* err;
 };
+uint32_t ttmc_task_max();
 mach_status launch_ttmc(const TtmcLaunch& L, bool compute_fp64, cudaStream_t st);
 template <typename T>
 mach_status launch_gram(const T* Z, int64_t L, int M, int64_t sl, int64_t sm, T* C, T* partial_scratch,
@@ -316,7 +318,8 @@ struct EigLaunch {
   void* U;
   double* Vout;
   double* theta;
-  int* info;
+  void* ctl;                   // >= 64 bytes of device scratch (split path)
+  unsigned long long* stats;   // device counters: calls, iterations, unconverged
 };
 template <typename T>
 mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st);

@@ -4,13 +4,16 @@
 // l.  The coin is value-independent, so the dense input is streamed once.
 //
 // GB300 design: persistent CTAs claim 32 KiB tiles of X through one atomic
-// counter (claim order = processing order, which keeps the look-back below
-// deadlock-free) and stream them into a 3-stage shared-memory ring with 1-D
-// TMA bulk copies completed on mbarriers.  While later tiles are in flight,
-// every thread evaluates Philox for 8 (FP32) or 4 (FP64) consecutive counters,
-// i.e. 32 / 16 consecutive entries, and the block compacts its kept entries
-// with a warp-shuffle scan; the tile's global offset comes from a single-pass
-// decoupled look-back over per-tile status words (bounded spin-waits).
+// counter and stream them into a 3-stage shared-memory ring with 1-D TMA bulk
+// copies completed on mbarriers.  Because the coin does not depend on the
+// data, a CTA evaluates Philox for a tile as soon as it claims it ("count
+// ahead"): each thread covers 8 (FP32) or 4 (FP64) consecutive Philox
+// counters, i.e. 32 / 16 consecutive entries; the keep masks and per-thread
+// prefixes are cached in shared memory and the tile's aggregate is published
+// at once.  When the tile's data has landed, the tile's global offset comes
+// from a decoupled look-back over the published per-tile status words
+// (bounded spin-waits) and the kept (l, value) pairs are written in order.
+// Philox is evaluated exactly once per counter.
 #include "mach_internal.cuh"
 
 namespace mach {
@@ -18,6 +21,7 @@ namespace mach {
 namespace {
 
 constexpr int kSampThreads = 256;
+constexpr int kSampWarps = kSampThreads / 32;
 constexpr int kSampStages = 3;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
@@ -47,16 +51,10 @@ struct SampleArgs {
   unsigned* err;
 };
 
-// Exclusive prefix of tile t (warp 0 of the block).  Publishes the tile's
-// aggregate first, then walks predecessors 32 at a time until it meets an
-// inclusive prefix; every wait is bounded.
-__device__ long long lookback(const SampleArgs& a, long long t, long long agg, int lane) {
+// Exclusive prefix of tile t (warp 0): walk predecessors 32 at a time until
+// an inclusive prefix is met; every wait is bounded.
+__device__ long long lookback(const SampleArgs& a, long long t, int lane) {
   unsigned long long* st = a.tile_status;
-  if (t == 0) {
-    if (lane == 0) st_release_u64(&st[0], kFlagPre | (unsigned long long)agg);
-    return 0;
-  }
-  if (lane == 0) st_release_u64(&st[t], kFlagAgg | (unsigned long long)agg);
   long long excl = 0;
   long long base = t - 1;
   long long spins = 0;
@@ -81,7 +79,6 @@ __device__ long long lookback(const SampleArgs& a, long long t, long long agg, i
     excl += warp_sum(val);
     base -= 32;
   }
-  if (lane == 0) st_release_u64(&st[t], kFlagPre | (unsigned long long)(excl + agg));
   return excl;
 }
 
@@ -92,7 +89,10 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
   V* stage_buf = reinterpret_cast<V*>(smem_raw);
   __shared__ uint64_t bars[kSampStages];
   __shared__ long long stage_tile[kSampStages];
-  __shared__ int warp_tot[kSampThreads / 32];
+  __shared__ uint32_t s_mask[kSampStages][kSampThreads];
+  __shared__ int s_pre[kSampStages][kSampThreads];   // per-thread exclusive prefix in the tile
+  __shared__ int s_agg[kSampStages];
+  __shared__ int warp_tot[kSampWarps];
   __shared__ long long s_excl;
 
   const int tid = threadIdx.x;
@@ -126,33 +126,14 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
     }
   };
 
-  if (tid == 0)
-    for (int s = 0; s < kSampStages; ++s) issue(s);
-
-  uint32_t parity = 0;
-  int s = 0;
-  for (;;) {
-    const bool ok = mbar_wait_bounded(&bars[s], (parity >> s) & 1u);
-    parity ^= 1u << s;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(a.err, DEV_TIMEOUT);
-      // drain: give every other stage a bounded chance to land before exit
-      for (int k = 1; k < kSampStages; ++k) {
-        const int s2 = (s + k) % kSampStages;
-        (void)mbar_wait_bounded(&bars[s2], (parity >> s2) & 1u);
-      }
-      break;
-    }
+  // All threads: evaluate the coin for the tile claimed into stage s, cache
+  // masks and prefixes, publish the aggregate (or, for tile 0, the prefix).
+  // Must be called after a __syncthreads that made stage_tile[s] visible.
+  auto count_ahead = [&](int s) {
     const long long t = stage_tile[s];
-    if (t >= a.num_tiles) break;
-
-    const V* buf = stage_buf + (size_t)s * C::kTile;
-    const int64_t e_tile = (int64_t)t * C::kTile;
-    const int64_t tile_n = min((int64_t)C::kTile, a.n - e_tile);
-    const int64_t n_staged = (int64_t)((((uint64_t)tile_n * sizeof(V)) & ~(uint64_t)15) / sizeof(V));
-    const int64_t e_thr = e_tile + (int64_t)tid * C::kEPT;
+    if (t >= a.num_tiles) return;  // uniform
+    const int64_t e_thr = (int64_t)t * C::kTile + (int64_t)tid * C::kEPT;
     const uint64_t q0 = (uint64_t)e_thr >> 2;
-
     uint32_t mask = 0;
 #pragma unroll
     for (int j = 0; j < C::kCPT; ++j) {
@@ -167,12 +148,8 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
       }
       mask |= b << (4 * j);
     }
-    {
-      const int64_t valid = a.n - e_thr;
-      if (valid < C::kEPT) mask &= valid <= 0 ? 0u : ((1u << valid) - 1u);
-    }
-
-    // block scan of per-thread counts
+    const int64_t valid = a.n - e_thr;
+    if (valid < C::kEPT) mask &= valid <= 0 ? 0u : ((1u << valid) - 1u);
     const int cnt = __popc(mask);
     int incl = cnt;
 #pragma unroll
@@ -184,17 +161,57 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
     __syncthreads();
     int warp_off = 0, blk = 0;
 #pragma unroll
-    for (int w = 0; w < kSampThreads / 32; ++w) {
+    for (int w = 0; w < kSampWarps; ++w) {
       const int v = warp_tot[w];
       warp_off += (w < warp) ? v : 0;
       blk += v;
     }
+    s_mask[s][tid] = mask;
+    s_pre[s][tid] = warp_off + incl - cnt;
+    if (tid == 0) {
+      s_agg[s] = blk;
+      st_release_u64(&a.tile_status[t], (t == 0 ? kFlagPre : kFlagAgg) | (unsigned long long)blk);
+    }
+    __syncthreads();  // warp_tot reuse
+  };
+
+  if (tid == 0)
+    for (int s = 0; s < kSampStages; ++s) issue(s);
+  __syncthreads();
+  for (int s = 0; s < kSampStages; ++s) count_ahead(s);
+
+  uint32_t parity = 0;
+  int s = 0;
+  for (;;) {
+    const bool ok = mbar_wait_bounded(&bars[s], (parity >> s) & 1u);
+    parity ^= 1u << s;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(a.err, DEV_TIMEOUT);
+      for (int k = 1; k < kSampStages; ++k) {
+        const int s2 = (s + k) % kSampStages;
+        (void)mbar_wait_bounded(&bars[s2], (parity >> s2) & 1u);
+      }
+      break;
+    }
+    const long long t = stage_tile[s];
+    if (t >= a.num_tiles) break;
+
     if (warp == 0) {
-      const long long e = lookback(a, t, blk, lane);
+      long long e = 0;
+      if (t > 0) {
+        e = lookback(a, t, lane);
+        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagPre | (unsigned long long)(e + s_agg[s]));
+      }
       if (lane == 0) s_excl = e;
     }
     __syncthreads();
-    long long pos = s_excl + warp_off + incl - cnt;
+    const V* buf = stage_buf + (size_t)s * C::kTile;
+    const int64_t e_tile = (int64_t)t * C::kTile;
+    const int64_t tile_n = min((int64_t)C::kTile, a.n - e_tile);
+    const int64_t n_staged = (int64_t)((((uint64_t)tile_n * sizeof(V)) & ~(uint64_t)15) / sizeof(V));
+    const int64_t e_thr = e_tile + (int64_t)tid * C::kEPT;
+    uint32_t mask = s_mask[s][tid];
+    long long pos = s_excl + s_pre[s][tid];
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -209,9 +226,11 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
       }
       ++pos;
     }
-    if (t == a.num_tiles - 1 && tid == 0) *a.out_count = s_excl + blk;
+    if (t == a.num_tiles - 1 && tid == 0) *a.out_count = s_excl + s_agg[s];
     __syncthreads();
     if (tid == 0) issue(s);
+    __syncthreads();
+    count_ahead(s);
     s = (s + 1 == kSampStages) ? 0 : s + 1;
   }
 }
@@ -226,11 +245,7 @@ mach_status launch_sampler_t(const void* x, int64_t n, uint64_t seed, uint64_t T
   MACH_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)(num_tiles + 1) * sizeof(unsigned long long), st));
   MACH_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));
   const size_t smem = kSampStages * C::kStageBytes;
-  static bool attr_set = false;
-  if (!attr_set) {
-    MACH_CUDA_TRY(cudaFuncSetAttribute(sample_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
+  MACH_CUDA_TRY(cudaFuncSetAttribute(sample_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<V>, kSampThreads, smem));
   if (per_sm < 1) per_sm = 1;

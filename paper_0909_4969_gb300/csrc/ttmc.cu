@@ -11,12 +11,16 @@
 // the cyclic mode order n+1, .., n-1.  Column order does not change the left
 // singular vectors; for mode d it is the natural order (r_1 .. r_{d-1}).
 //
-// GB300 mapping: one warp per task (a segment of <= E entries of one row);
-// lanes own fibres for the leaf level (factor rows of the leaf mode staged in
-// shared memory with one TMA bulk copy per CTA), the warp then owns the row's
-// J_n accumulators (lane j holds columns j, j+32, ..) and folds the 32 fibre
-// vectors in from shared memory.  A row split over several tasks is reduced in
-// task order by a fix-up kernel, so results are deterministic.
+// GB300 mapping: one warp per task (a segment of <= E entries of one row).
+// The task's values and leaf indices are staged into the warp's shared-memory
+// buffer with two 1-D TMA bulk copies completed on a per-warp mbarrier (one
+// elected lane issues them; the warp waits on the phase).  Lanes then own
+// fibres for the leaf level, reading entries from shared memory and factor
+// rows of the leaf mode from shared memory (small factors, staged once per
+// CTA) or through L1.  The warp owns the row's J_n accumulators (lane j holds
+// columns j, j+32, ..) and folds the 32 fibre vectors in from shared memory.
+// A row split over several tasks is reduced in task order by a fix-up kernel,
+// so results are deterministic.
 #include "mach_internal.cuh"
 
 namespace mach {
@@ -25,8 +29,9 @@ namespace {
 
 constexpr int kTtmcWarps = 8;
 constexpr int kTtmcThreads = 32 * kTtmcWarps;
-constexpr int kAcc = kMaxJ / 32;   // 32 row accumulators per lane
-constexpr int kSQ = 8;             // level-2 accumulators per lane (d = 4)
+constexpr int kSQ = 8;                 // level-2 accumulators per lane (d = 4)
+constexpr uint32_t kTaskMax = 2048;    // entries per task (shared-memory staging)
+constexpr uint32_t kLeafStageMax = 16 * 1024;
 
 template <typename T>
 struct TtmcArgs {
@@ -44,36 +49,51 @@ struct TtmcArgs {
   int r_leaf, r_mid0, r_mid1;
   int J;                      // row length of Y
   int Q;                      // level-2 width: d == 4: r_mid1 * r_leaf, else J
-  uint32_t leaf_bytes_staged; // 0 = read A_leaf from global
+  uint32_t leaf_bytes_staged; // 0 = read A_leaf through L1
   T* Y;                       // I_n x J
   T* partial;                 // ntask x J
+  unsigned* err;
 };
 
-template <typename V, typename T, int D>
+// Per-warp staging buffer: values (padded) then leaf indices (padded).
+template <typename V>
+struct WarpStage {
+  static constexpr uint32_t kValBytes = (kTaskMax + 16) * sizeof(V);
+  static constexpr uint32_t kLeafBytes = (kTaskMax + 16) * 2;
+  static constexpr uint32_t kBytes = kValBytes + kLeafBytes;
+};
+
+template <typename V, typename T, int D, int ACC, int RLM>
 __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bar;
-  __shared__ T sz[kTtmcWarps][32][kMaxRank + 1];
+  __shared__ uint64_t bar_leaf;
+  __shared__ uint64_t bar_warp[kTtmcWarps];
+  __shared__ T sz[kTtmcWarps][32][RLM + 1];
   __shared__ uint32_t smid[kTtmcWarps][32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const V* val = static_cast<const V*>(a.val);
+  unsigned char* wbuf = smem_raw + a.leaf_bytes_staged + (size_t)warp * WarpStage<V>::kBytes;
+  V* sval = reinterpret_cast<V*>(wbuf);
+  uint16_t* sleaf = reinterpret_cast<uint16_t*>(wbuf + WarpStage<V>::kValBytes);
 
-  // Stage the leaf factor (the hottest gather) in shared memory.
+  if (tid == 0) {
+    mbar_init(&bar_leaf, 1);
+    for (int w = 0; w < kTtmcWarps; ++w) mbar_init(&bar_warp[w], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // Stage the leaf factor (the hottest gather) in shared memory when small.
   const T* Aleaf = a.A_leaf;
   if (a.leaf_bytes_staged) {
     T* sA = reinterpret_cast<T*>(smem_raw);
     if (tid == 0) {
-      mbar_init(&bar, 1);
-      fence_mbar_init();
+      mbar_arrive_expect_tx(&bar_leaf, a.leaf_bytes_staged);
+      bulk_g2s(sA, a.A_leaf, a.leaf_bytes_staged, &bar_leaf);
     }
-    __syncthreads();
-    if (tid == 0) {
-      mbar_arrive_expect_tx(&bar, a.leaf_bytes_staged);
-      bulk_g2s(sA, a.A_leaf, a.leaf_bytes_staged, &bar);
-    }
-    if (!mbar_wait_bounded(&bar, 0)) {
-      return;  // the copy never landed; Y is left unwritten (host sees garbage, never a hang)
+    if (!mbar_wait_bounded(&bar_leaf, 0)) {
+      if (tid == 0) atomicOr(a.err, DEV_TIMEOUT);
+      return;
     }
     Aleaf = sA;
   }
@@ -81,9 +101,10 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
   const int rl = a.r_leaf;
   const int Q = a.Q;
   const int SQ = (Q + 31) >> 5;
-  int qa[kSQ > kAcc ? kSQ : kAcc], qb[kSQ > kAcc ? kSQ : kAcc];
+  constexpr int NQ = D == 4 ? kSQ : ACC;
+  int qa[NQ], qb[NQ];
 #pragma unroll
-  for (int s = 0; s < (D == 4 ? kSQ : kAcc); ++s) {
+  for (int s = 0; s < NQ; ++s) {
     const int q = lane + 32 * s;
     qa[s] = q / rl;
     qb[s] = q - qa[s] * rl;
@@ -93,17 +114,29 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
   const uint32_t nfib = *a.d_nfib;
   const int gwarp = blockIdx.x * kTtmcWarps + warp;
   const int nwarps = gridDim.x * kTtmcWarps;
+  uint32_t phase = 0;
 
   for (uint32_t t = gwarp; t < ntask; t += nwarps) {
     const int4 tk = a.tasks[t];
     const int row = tk.x;
     const uint32_t e0 = (uint32_t)tk.y, e1 = (uint32_t)tk.z;
-    T acc[kAcc];
+    // stage entries [e0, e1): round the start down to a 16-byte boundary of both arrays
+    const uint32_t ealign = 16 / sizeof(uint16_t);   // 8 entries (also a multiple of 16 B of V)
+    const uint32_t base = e0 & ~(ealign - 1);
+    const uint32_t nstage = ((e1 - base) + ealign - 1) & ~(ealign - 1);
+    if (lane == 0) {
+      const uint32_t vb = nstage * (uint32_t)sizeof(V), lb = nstage * 2u;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar_warp[warp], vb + lb);
+      bulk_g2s(sval, val + base, vb, &bar_warp[warp]);
+      bulk_g2s(sleaf, a.leaf + base, lb, &bar_warp[warp]);
+    }
+    T acc[ACC];
 #pragma unroll
-    for (int s = 0; s < kAcc; ++s) acc[s] = T(0);
-    T w[kSQ];
+    for (int s = 0; s < ACC; ++s) acc[s] = T(0);
+    T w[D == 4 ? kSQ : 1];
 #pragma unroll
-    for (int s = 0; s < kSQ; ++s) w[s] = T(0);
+    for (int s = 0; s < (D == 4 ? kSQ : 1); ++s) w[s] = T(0);
     uint32_t cur_a1 = 0xffffffffu;
 
     auto flush_w = [&]() {
@@ -115,13 +148,19 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
             const T m = arow[r1];
 #pragma unroll
             for (int s = 0; s < kSQ; ++s)
-              if (s < SQ && r1 * SQ + s < kAcc) acc[r1 * SQ + s] += m * w[s];
+              if (s < SQ && r1 * SQ + s < ACC) acc[r1 * SQ + s] += m * w[s];
           }
         }
 #pragma unroll
-        for (int s = 0; s < kSQ; ++s) w[s] = T(0);
+        for (int s = 0; s < (D == 4 ? kSQ : 1); ++s) w[s] = T(0);
       }
     };
+
+    if (!mbar_wait_bounded(&bar_warp[warp], phase)) {
+      if (lane == 0) atomicOr(a.err, DEV_TIMEOUT);
+      return;
+    }
+    phase ^= 1u;
 
     for (uint32_t fb = (uint32_t)tk.w;; fb += 32) {
       const uint32_t f = fb + lane;
@@ -133,24 +172,24 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
       const bool valid = f < nfib && fs < e1;
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       if (!vm) break;
-      T z[kMaxRank];
+      T z[RLM];
 #pragma unroll
-      for (int b = 0; b < kMaxRank; ++b) z[b] = T(0);
+      for (int b = 0; b < RLM; ++b) z[b] = T(0);
       uint32_t mid = 0;
       if (valid) {
-        const uint32_t s0 = fs > e0 ? fs : e0;
-        const uint32_t s1 = fe < e1 ? fe : e1;
+        const uint32_t s0 = (fs > e0 ? fs : e0) - base;
+        const uint32_t s1 = (fe < e1 ? fe : e1) - base;
         for (uint32_t e = s0; e < s1; ++e) {
-          const T v = (T)val[e];
-          const T* ar = Aleaf + (size_t)a.leaf[e] * rl;
+          const T v = (T)sval[e];
+          const T* ar = Aleaf + (size_t)sleaf[e] * rl;
 #pragma unroll
-          for (int b = 0; b < kMaxRank; ++b)
+          for (int b = 0; b < RLM; ++b)
             if (b < rl) z[b] += v * ar[b];
         }
         mid = a.fib_mid[f];
       }
 #pragma unroll
-      for (int b = 0; b < kMaxRank; ++b)
+      for (int b = 0; b < RLM; ++b)
         if (b < rl) sz[warp][lane][b] = z[b];
       smid[warp][lane] = mid;
       __syncwarp();
@@ -158,15 +197,11 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
       for (int j = 0; j < nv; ++j) {
         const T* zj = sz[warp][j];
         if (D == 2) {
-#pragma unroll
-          for (int s = 0; s < kAcc; ++s) {
-            const int q = lane + 32 * s;
-            if (q < rl) acc[s] += zj[q];
-          }
+          if (lane < rl) acc[0] += zj[lane];
         } else if (D == 3) {
           const T* arow = a.A_mid0 + (size_t)smid[warp][j] * a.r_mid0;
 #pragma unroll
-          for (int s = 0; s < kAcc; ++s)
+          for (int s = 0; s < ACC; ++s)
             if (lane + 32 * s < Q) acc[s] += arow[qa[s]] * zj[qb[s]];
         } else {
           const uint32_t m = smid[warp][j];
@@ -178,7 +213,7 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
           const T* arow = a.A_mid1 + (size_t)a2 * a.r_mid1;
 #pragma unroll
           for (int s = 0; s < kSQ; ++s)
-            if (lane + 32 * s < Q) w[s] += arow[qa[s]] * zj[qb[s]];
+            if (s < SQ && lane + 32 * s < Q) w[s] += arow[qa[s]] * zj[qb[s]];
         }
       }
       __syncwarp();
@@ -194,17 +229,18 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
 #pragma unroll
           for (int s = 0; s < kSQ; ++s) {
             const int q = lane + 32 * s;
-            if (s < SQ && q < Q && r1 * SQ + s < kAcc) dst[r1 * Q + q] = acc[r1 * SQ + s];
+            if (s < SQ && q < Q && r1 * SQ + s < ACC) dst[r1 * Q + q] = acc[r1 * SQ + s];
           }
         }
       }
     } else {
 #pragma unroll
-      for (int s = 0; s < kAcc; ++s) {
+      for (int s = 0; s < ACC; ++s) {
         const int q = lane + 32 * s;
         if (q < a.J) dst[q] = acc[s];
       }
     }
+    __syncwarp();   // the staging buffer is reused by the next task
   }
 }
 
@@ -223,9 +259,9 @@ __global__ void ttmc_fixup_kernel(const uint32_t* __restrict__ row_task, int J, 
 
 }  // namespace
 
+uint32_t ttmc_task_max() { return kTaskMax; }
 
-
-template <typename V, typename T, int D>
+template <typename V, typename T, int D, int ACC, int RLM>
 static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   TtmcArgs<T> a;
   a.val = L.val;
@@ -246,20 +282,22 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   a.Q = D == 4 ? L.r_mid1 * L.r_leaf : L.J;
   a.Y = static_cast<T*>(L.Y);
   a.partial = static_cast<T*>(L.partial);
+  a.err = L.err;
   const size_t leaf_bytes = (size_t)L.I_leaf * L.r_leaf * sizeof(T);
   const size_t staged = (leaf_bytes + 15) & ~(size_t)15;
-  a.leaf_bytes_staged = staged <= 96 * 1024 ? (uint32_t)staged : 0u;
-  const size_t smem = a.leaf_bytes_staged;
-  MACH_CUDA_TRY(cudaFuncSetAttribute(ttmc_kernel<V, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(smem > 0 ? smem : 1)));
+  a.leaf_bytes_staged = staged <= kLeafStageMax ? (uint32_t)staged : 0u;
+  const size_t smem = a.leaf_bytes_staged + (size_t)kTtmcWarps * WarpStage<V>::kBytes;
+  MACH_CUDA_TRY(cudaFuncSetAttribute(ttmc_kernel<V, T, D, ACC, RLM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
   int per_sm = 0;
-  MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttmc_kernel<V, T, D>, kTtmcThreads, smem));
+  MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttmc_kernel<V, T, D, ACC, RLM>,
+                                                              kTtmcThreads, smem));
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms() * per_sm;
   const int64_t need = ceil_div(L.ntask_cap, kTtmcWarps);
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  ttmc_kernel<V, T, D><<<(unsigned)grid, kTtmcThreads, smem, st>>>(a);
+  ttmc_kernel<V, T, D, ACC, RLM><<<(unsigned)grid, kTtmcThreads, smem, st>>>(a);
   MACH_LAUNCH_CHECK();
   ttmc_fixup_kernel<T><<<L.nrows, 128, 0, st>>>(L.row_task, L.J, static_cast<const T*>(L.partial),
                                                  static_cast<T*>(L.Y));
@@ -267,14 +305,32 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   return MACH_OK;
 }
 
+template <typename V, typename T, int D, int ACC>
+static mach_status launch_ttmc_rl(const TtmcLaunch& L, cudaStream_t st) {
+  if (L.r_leaf <= 4) return launch_ttmc_t<V, T, D, ACC, 4>(L, st);
+  if (L.r_leaf <= 8) return launch_ttmc_t<V, T, D, ACC, 8>(L, st);
+  return launch_ttmc_t<V, T, D, ACC, 16>(L, st);
+}
+
 template <typename V, typename T>
 static mach_status launch_ttmc_vt(const TtmcLaunch& L, cudaStream_t st) {
-  switch (L.d) {
-    case 2: return launch_ttmc_t<V, T, 2>(L, st);
-    case 3: return launch_ttmc_t<V, T, 3>(L, st);
-    case 4: return launch_ttmc_t<V, T, 4>(L, st);
-    default: return MACH_EINVAL;
+  if (L.d == 2) return launch_ttmc_rl<V, T, 2, 1>(L, st);
+  if (L.d == 3) {
+    const int need = (L.J + 31) / 32;
+    if (need <= 1) return launch_ttmc_rl<V, T, 3, 1>(L, st);
+    if (need <= 2) return launch_ttmc_rl<V, T, 3, 2>(L, st);
+    if (need <= 4) return launch_ttmc_rl<V, T, 3, 4>(L, st);
+    return launch_ttmc_rl<V, T, 3, 8>(L, st);
   }
+  if (L.d == 4) {
+    const int Q = L.r_mid1 * L.r_leaf;
+    const int need = L.r_mid0 * ((Q + 31) / 32);
+    if (need <= 4) return launch_ttmc_rl<V, T, 4, 4>(L, st);
+    if (need <= 8) return launch_ttmc_rl<V, T, 4, 8>(L, st);
+    if (need <= 16) return launch_ttmc_rl<V, T, 4, 16>(L, st);
+    return launch_ttmc_rl<V, T, 4, 32>(L, st);
+  }
+  return MACH_EINVAL;
 }
 
 mach_status launch_ttmc(const TtmcLaunch& L, bool compute_fp64, cudaStream_t st) {

@@ -37,6 +37,8 @@ SIGNATURES = {
     "mach_sample_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "mach_sample_fibers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i64p]),
     "mach_sample_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "mach_sample_stats": (ctypes.c_int, [ctypes.c_void_p, _c_i64p, _c_i64p, _c_i64p,
+                                         ctypes.POINTER(ctypes.c_uint)]),
     "mach_hooi": (ctypes.c_int, [ctypes.c_void_p, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, ctypes.c_void_p,
                                  ctypes.c_int, ctypes.c_void_p]),
     "mach_core": (ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_pp, ctypes.c_void_p, ctypes.c_void_p]),
@@ -188,6 +190,14 @@ class Sample:
         _check("mach_core", self._lib.mach_core(self.handle, _int(ranks), _ptrs(factors),
                                                 ctypes.c_void_p(G.data_ptr()), _stream(stream)))
         return G
+
+    def stats(self) -> dict:
+        """Eigensolver calls / iterations / unconverged solves and device status bits."""
+        c, it, un = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        fl = ctypes.c_uint()
+        _check("mach_sample_stats", self._lib.mach_sample_stats(self.handle, ctypes.byref(c), ctypes.byref(it),
+                                                                ctypes.byref(un), ctypes.byref(fl)))
+        return {"eig_calls": c.value, "eig_iters": it.value, "eig_unconverged": un.value, "flags": fl.value}
 
     def free(self):
         if self._h is not None:

@@ -70,7 +70,7 @@ def tucker_numpy(spec: TuckerSpec):
         E = rng.standard_normal(spec.dims)
         E *= spec.noise * np.linalg.norm(X) / np.linalg.norm(E)
         X = X + E
-    return X.astype(spec.dtype), G, Us
+    return np.ascontiguousarray(X.astype(spec.dtype)), G, Us
 
 
 def tucker_torch(spec: TuckerSpec, device="cuda", chunk_elems: int = 1 << 27):
@@ -238,7 +238,7 @@ class StreamState:
         X = _expand(self.G, self.Us)
         E = self.rng.standard_normal(self.dims)
         E *= noise * np.linalg.norm(X) / np.linalg.norm(E)
-        return (X + E).astype(dtype)
+        return np.ascontiguousarray((X + E).astype(dtype))
 
 
 def tucker_for_dims(dims, ranks, noise: float, seed: int, dtype="float32", core="gaussian"):

@@ -26,6 +26,8 @@ def run_both(X, ranks, p, seed, sweeps, prec):
     torch.cuda.synchronize()
     G_g = G.cpu().numpy()
     A_g = [a.cpu().numpy() for a in A]
+    st = s.stats()
+    assert st["flags"] == 0, st
     s.free()
     return S, G_o, A_o, G_g, A_g, xd
 
