@@ -639,7 +639,7 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.r = r;
   e.b = b;
   e.maxit = maxit;
-  e.tol = sizeof(T) == 8 ? 1e-13 : 2e-6;
+  e.tol = sizeof(T) == 8 ? 1e-14 : 2e-6;
   e.V = w.V.ptr;
   e.W = w.W.ptr;
   e.U = w.U.ptr;

@@ -384,7 +384,7 @@ __device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, doubl
     double worst = 0.0;
     for (int j = 0; j < r; ++j) worst = fmax(worst, sqrt(sh.res[j]));
     const double rel = th0 > 0.0 ? worst / th0 : 0.0;
-    const bool floor_hit = rel < 100.0 * tol && rel > 0.5 * (*prev_worst);
+    const bool floor_hit = rel < 10.0 * tol && rel > 0.5 * (*prev_worst);
     sh.conv = (th0 == 0.0) || (rel <= tol) || floor_hit;
     *prev_worst = rel;
   }

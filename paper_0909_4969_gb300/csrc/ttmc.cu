@@ -307,8 +307,11 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
 
 template <typename V, typename T, int D, int ACC>
 static mach_status launch_ttmc_rl(const TtmcLaunch& L, cudaStream_t st) {
+  // leaf-rank widths: exact for the common ranks 4, 5, 8, 10, padded otherwise
   if (L.r_leaf <= 4) return launch_ttmc_t<V, T, D, ACC, 4>(L, st);
+  if (L.r_leaf == 5) return launch_ttmc_t<V, T, D, ACC, 5>(L, st);
   if (L.r_leaf <= 8) return launch_ttmc_t<V, T, D, ACC, 8>(L, st);
+  if (L.r_leaf <= 10) return launch_ttmc_t<V, T, D, ACC, 10>(L, st);
   return launch_ttmc_t<V, T, D, ACC, 16>(L, st);
 }
 
