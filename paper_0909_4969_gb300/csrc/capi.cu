@@ -228,8 +228,12 @@ Cyc cyc(int d, int n) {
   return c;
 }
 
-int block_size_for(int M, int r) {
-  int b = std::max(r + 4, 2 * r);
+// Block width of the subspace iteration: the leading r eigenvectors converge
+// like (lambda_{b+1} / lambda_r)^k, so a wider block pays off when the
+// spectrum is crowded near r.  Warm-started HOOI updates use at least 16
+// columns; the cold HOSVD start always uses the full 32.
+int block_size_for(int M, int r, bool cold) {
+  int b = cold ? 32 : std::max(std::max(2 * r, r + 8), 16);
   b = std::min(b, 32);
   return std::min(b, M);
 }
@@ -631,7 +635,7 @@ template <typename T>
 mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, int J, bool jroute, bool warm,
                          int maxit, double* fac_out, cudaStream_t st) {
   const int M = jroute ? J : I;
-  const int b = block_size_for(M, r);
+  const int b = block_size_for(M, r, !warm);
   MACH_TRY(launch_start_block<T>(static_cast<const T*>(w.Y.ptr), static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
                                  jroute, warm, static_cast<T*>(w.V.ptr), 0x1000u + (uint32_t)n, st));
   EigLaunch e;
