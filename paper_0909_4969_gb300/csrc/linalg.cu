@@ -224,8 +224,10 @@ __device__ void block_reduce_vec(T (&v)[NV], T* red /* [warps][NV] */, T* out) {
 }
 
 constexpr int kEigThreads = 256;
+constexpr int kEigWarps = kEigThreads / 32;
 constexpr int kBMax = 32;
 constexpr int kEigSmallMax = 256;   // larger Grams take the split (multi-CTA) path
+constexpr int kChunk = 32;          // rows per shared-memory chunk in streamed reductions
 
 // Shared-memory state of one Rayleigh-Ritz step.
 template <typename T>
@@ -234,9 +236,11 @@ struct RRShared {
   T Qm[kBMax * kBMax];
   T G[kBMax * kBMax];
   T cs[kBMax * 2];
+  T xa[kChunk * kBMax];   // row chunk of the left operand
+  T xb[kChunk * kBMax];   // row chunk of the right operand
   int pq[kBMax * 2];
   int perm[kBMax];
-  double red[(kEigThreads / 32) * kBMax];
+  double red[kEigWarps * kBMax];
   double res[kBMax];
   int conv;
 };
@@ -250,11 +254,11 @@ struct EigCtl {
 
 template <typename T>
 struct EigArgs {
-  const T* C;          // M x M symmetric (row-major)
+  const T* C;          // M x M symmetric (row-major), global
   int M, r, b;
-  T* V;                // M x b, holds V0 on entry
-  T* W;                // M x b
-  T* U;                // M x b
+  T* V;                // M x b, holds V0 on entry (global)
+  T* W;                // M x b (global scratch)
+  T* U;                // M x b (global scratch)
   double* Vout;        // M x r, FP64 leading eigenvectors (row-major)
   double* theta;       // r eigenvalues, FP64, descending
   int maxit;
@@ -263,39 +267,84 @@ struct EigArgs {
   unsigned long long* stats;  // [0] calls, [1] iterations, [2] unconverged
 };
 
-// W[:, :ncols] = C V[:, :ncols] for an M x b block; all threads of the CTA.
+// W[:, :ncols] = C V[:, :ncols] (row stride b for V and W).  One warp per row
+// of C, lanes over the columns of C; rows [row0, row1) step by `rstep`.
 template <typename T>
-__device__ void symm_times_block(const T* C, const T* V, T* W, int M, int b, int ncols) {
-  for (int o = threadIdx.x; o < M * ncols; o += blockDim.x) {
-    const int i = o / ncols, j = o - (o / ncols) * ncols;
-    const T* crow = C + (size_t)i * M;
-    T s = T(0);
-    for (int k = 0; k < M; ++k) s += crow[k] * V[(size_t)k * b + j];
-    W[(size_t)i * b + j] = s;
+__device__ void cv_rows(const T* C, int ldc, const T* V, T* W, int M, int b, int ncols, int row0, int row1,
+                        int warp, int nwarps) {
+  const int lane = threadIdx.x & 31;
+  for (int i = row0 + warp; i < row1; i += nwarps) {
+    const T* crow = C + (size_t)i * ldc;
+    T s[kBMax];
+#pragma unroll
+    for (int j = 0; j < kBMax; ++j) s[j] = T(0);
+    for (int k = lane; k < M; k += 32) {
+      const T c = crow[k];
+      const T* vr = V + (size_t)k * b;
+#pragma unroll
+      for (int j = 0; j < kBMax; ++j)
+        if (j < ncols) s[j] += c * vr[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kBMax; ++j) {
+      if (j < ncols) {
+        const T v = warp_sum(s[j]);
+        if (lane == 0) W[(size_t)i * b + j] = v;
+      }
+    }
   }
 }
 
-// Orthonormalise the columns of X (M x b, row-major) in place, in the path's
-// precision T: column scaling, then Cholesky QR twice (X <- X R^-1).  Used on
-// blocks whose columns are already nearly orthogonal (C times Ritz vectors),
-// so the Gram is well conditioned after scaling.
+// H = X^T Y (b x b, row-major ld kBMax) for M x b row-major X, Y; rows are
+// streamed through shared memory in chunks (works for global or shared
+// sources).  Thread t owns the entries t, t + 256, .. of H.
 template <typename T>
-__device__ void orth_block(T* X, int M, int b, T* G) {
-  for (int pass = 0; pass < 3; ++pass) {
-    for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
-      const int p = pidx / b, q = pidx - (pidx / b) * b;
-      if (q < p) continue;
-      T s = T(0);
-      for (int i = 0; i < M; ++i) s += X[(size_t)i * b + p] * X[(size_t)i * b + q];
-      G[p * kBMax + q] = s;
-      G[q * kBMax + p] = s;
+__device__ void gram_xty(const T* X, const T* Y, int M, int b, T* H, RRShared<T>& sh) {
+  T acc[(kBMax * kBMax) / kEigThreads];
+#pragma unroll
+  for (int k = 0; k < (kBMax * kBMax) / kEigThreads; ++k) acc[k] = T(0);
+  for (int c0 = 0; c0 < M; c0 += kChunk) {
+    const int nr = min(kChunk, M - c0);
+    for (int o = threadIdx.x; o < nr * b; o += blockDim.x) {
+      sh.xa[o] = X[(size_t)c0 * b + o];
+      sh.xb[o] = Y[(size_t)c0 * b + o];
     }
     __syncthreads();
+#pragma unroll
+    for (int k = 0; k < (kBMax * kBMax) / kEigThreads; ++k) {
+      const int e = threadIdx.x + k * kEigThreads;
+      if (e < b * b) {
+        const int p = e / b, q = e - (e / b) * b;
+        T s = acc[k];
+        for (int i = 0; i < nr; ++i) s += sh.xa[i * b + p] * sh.xb[i * b + q];
+        acc[k] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < (kBMax * kBMax) / kEigThreads; ++k) {
+    const int e = threadIdx.x + k * kEigThreads;
+    if (e < b * b) H[(e / b) * kBMax + (e - (e / b) * b)] = acc[k];
+  }
+  __syncthreads();
+}
+
+// Orthonormalise the columns of X (M x b) in place in precision T: column
+// scaling, then Cholesky QR twice (X <- X R^-1).  Used on blocks whose
+// columns are already nearly orthogonal (C times Ritz vectors), so the Gram
+// is well conditioned after scaling.
+template <typename T>
+__device__ void orth_block(T* X, int M, int b, RRShared<T>& sh) {
+  for (int pass = 0; pass < 3; ++pass) {
+    gram_xty<T>(X, X, M, b, sh.G, sh);
     if (pass == 0) {
-      for (int o = threadIdx.x; o < M * b; o += blockDim.x) {
-        const int j = o - (o / b) * b;
-        const T nrm = sqrt(G[j * kBMax + j]);
-        X[o] = nrm > T(0) ? X[o] / nrm : T(0);
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        T* xr = X + (size_t)i * b;
+        for (int j = 0; j < b; ++j) {
+          const T nrm = sqrt(sh.G[j * kBMax + j]);
+          xr[j] = nrm > T(0) ? xr[j] / nrm : T(0);
+        }
       }
       __syncthreads();
       continue;
@@ -304,25 +353,27 @@ __device__ void orth_block(T* X, int M, int b, T* G) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       for (int j = 0; j < b; ++j) {
-        T djj = G[j * kBMax + j];
+        T djj = sh.G[j * kBMax + j];
         djj = djj > T(0) ? sqrt(djj) : T(1e-30);
         __syncwarp();
-        if (lane == 0) G[j * kBMax + j] = djj;
-        for (int c = j + 1 + lane; c < b; c += 32) G[j * kBMax + c] /= djj;
+        if (lane == 0) sh.G[j * kBMax + j] = djj;
+        for (int c = j + 1 + lane; c < b; c += 32) sh.G[j * kBMax + c] /= djj;
         __syncwarp();
         for (int c = j + 1 + lane; c < b; c += 32)
-          for (int c2 = c; c2 < b; ++c2) G[c * kBMax + c2] -= G[j * kBMax + c] * G[j * kBMax + c2];
+          for (int c2 = c; c2 < b; ++c2) sh.G[c * kBMax + c2] -= sh.G[j * kBMax + c] * sh.G[j * kBMax + c2];
         __syncwarp();
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
-      T* xr = X + (size_t)i * b;
+      T xr[kBMax];
+      for (int j = 0; j < b; ++j) xr[j] = X[(size_t)i * b + j];
       for (int j = 0; j < b; ++j) {
         T v = xr[j];
-        for (int k = 0; k < j; ++k) v -= xr[k] * G[k * kBMax + j];
-        xr[j] = v / G[j * kBMax + j];
+        for (int k = 0; k < j; ++k) v -= xr[k] * sh.G[k * kBMax + j];
+        xr[j] = v / sh.G[j * kBMax + j];
       }
+      for (int j = 0; j < b; ++j) X[(size_t)i * b + j] = xr[j];
     }
     __syncthreads();
   }
@@ -332,17 +383,19 @@ __device__ void orth_block(T* X, int M, int b, T* G) {
 // H = V^T W, H = Q Theta Q^T (Jacobi), U = V Q (Ritz vectors), W <- W Q,
 // residuals ||W_j - theta_j U_j|| of the leading r.  Converged when every
 // residual is below tol * theta_1, or when the residual has reached the
-// arithmetic's floor (below 100 tol and no longer halving).  If not
+// arithmetic's floor (below 10 tol and no longer halving).  If not
 // converged, V <- orth(W) for the next power step.  Returns converged.
 template <typename T>
 __device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, double* prev_worst, RRShared<T>& sh) {
-  for (int pidx = threadIdx.x; pidx < b * b; pidx += blockDim.x) {
-    const int p = pidx / b, q = pidx - (pidx / b) * b;
-    if (q < p) continue;
-    T s = T(0);
-    for (int i = 0; i < M; ++i) s += V[(size_t)i * b + p] * W[(size_t)i * b + q];
-    sh.H[p * kBMax + q] = s;
-    sh.H[q * kBMax + p] = s;
+  gram_xty<T>(V, W, M, b, sh.H, sh);
+  // symmetrise (rounding) before Jacobi
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int p = e / b, q = e - (e / b) * b;
+    if (p < q) {
+      const T avg = (sh.H[p * kBMax + q] + sh.H[q * kBMax + p]) * T(0.5);
+      sh.H[p * kBMax + q] = avg;
+      sh.H[q * kBMax + p] = avg;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -350,35 +403,31 @@ __device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, doubl
     sort_desc_warp<T>(sh.H, b, kBMax, sh.perm);
   }
   __syncthreads();
+  double loc[kBMax];
+  for (int j = 0; j < kBMax; ++j) loc[j] = 0.0;
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    T u[kBMax], wq[kBMax];
+    T vr[kBMax], wr[kBMax];
+    for (int k = 0; k < b; ++k) {
+      vr[k] = V[(size_t)i * b + k];
+      wr[k] = W[(size_t)i * b + k];
+    }
     for (int j = 0; j < b; ++j) {
       const int pj = sh.perm[j];
       T su = T(0), sw = T(0);
       for (int k = 0; k < b; ++k) {
-        su += V[(size_t)i * b + k] * sh.Qm[k * kBMax + pj];
-        sw += W[(size_t)i * b + k] * sh.Qm[k * kBMax + pj];
+        const T q = sh.Qm[k * kBMax + pj];
+        su += vr[k] * q;
+        sw += wr[k] * q;
       }
-      u[j] = su;
-      wq[j] = sw;
-    }
-    for (int j = 0; j < b; ++j) {
-      U[(size_t)i * b + j] = u[j];
-      W[(size_t)i * b + j] = wq[j];
-    }
-  }
-  __syncthreads();
-  {
-    double loc[kBMax];
-    for (int j = 0; j < kBMax; ++j) loc[j] = 0.0;
-    for (int i = threadIdx.x; i < M; i += blockDim.x)
-      for (int j = 0; j < r; ++j) {
-        const double th = (double)sh.H[sh.perm[j] * kBMax + sh.perm[j]];
-        const double d = (double)W[(size_t)i * b + j] - th * (double)U[(size_t)i * b + j];
+      U[(size_t)i * b + j] = su;
+      W[(size_t)i * b + j] = sw;
+      if (j < r) {
+        const double d = (double)sw - (double)sh.H[pj * kBMax + pj] * (double)su;
         loc[j] += d * d;
       }
-    block_reduce_vec<double, kBMax>(loc, sh.red, sh.res);
+    }
   }
+  block_reduce_vec<double, kBMax>(loc, sh.red, sh.res);
   if (threadIdx.x == 0) {
     const double th0 = fabs((double)sh.H[sh.perm[0] * kBMax + sh.perm[0]]);
     double worst = 0.0;
@@ -392,7 +441,7 @@ __device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, doubl
   if (sh.conv) return true;
   for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = W[o];
   __syncthreads();
-  orth_block<T>(V, M, b, sh.G);
+  orth_block<T>(V, M, b, sh);
   return false;
 }
 
@@ -417,9 +466,11 @@ __device__ void final_rr(const T* U, const T* W, int M, int b, int r, double* Vo
   }
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    double ur[kMaxRank];
+    for (int k = 0; k < r; ++k) ur[k] = (double)U[(size_t)i * b + k];
     for (int j = 0; j < r; ++j) {
       double s = 0.0;
-      for (int k = 0; k < r; ++k) s += (double)U[(size_t)i * b + k] * Q64[k * kBMax + sh.perm[j]];
+      for (int k = 0; k < r; ++k) s += ur[k] * Q64[k * kBMax + sh.perm[j]];
       Vout[(size_t)i * r + j] = s;
     }
   }
@@ -427,31 +478,74 @@ __device__ void final_rr(const T* U, const T* W, int M, int b, int r, double* Vo
   __syncthreads();
 }
 
-// Fused path (one CTA, small M): orth, iterate power step + Rayleigh-Ritz,
-// final FP64 Rayleigh-Ritz.
+// Shared-memory plan of the fused kernel: V, W, U and then C when they fit
+// in `budget` bytes of dynamic shared memory (mode 2: all in smem, 1: V/W/U
+// only, 0: everything stays in global memory).
+struct EigSmemPlan {
+  int mode;
+  size_t bytes;
+};
+
+inline EigSmemPlan eig_smem_plan(int M, int b, size_t elem, size_t budget) {
+  EigSmemPlan p;
+  const size_t vwu = (size_t)3 * M * b * elem;
+  const size_t c = (size_t)M * M * elem;
+  if (vwu + c <= budget) {
+    p.mode = 2;
+    p.bytes = vwu + c;
+  } else if (vwu <= budget) {
+    p.mode = 1;
+    p.bytes = vwu;
+  } else {
+    p.mode = 0;
+    p.bytes = 0;
+  }
+  return p;
+}
+
+// Fused path (one CTA, M <= kEigSmallMax): operands in shared memory, power
+// step + Rayleigh-Ritz until converged, final FP64 Rayleigh-Ritz.
 template <typename T>
-__global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a) {
+__global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a, int smem_mode) {
+  extern __shared__ __align__(16) unsigned char eig_smem[];
   __shared__ RRShared<T> sh;
   __shared__ double H64[kBMax * kBMax];
   __shared__ double Q64[kBMax * kBMax];
   __shared__ double cs64[kBMax * 2];
   __shared__ double prev;
   const int M = a.M, b = a.b, r = a.r;
+  T* V = a.V;
+  T* W = a.W;
+  T* U = a.U;
+  const T* C = a.C;
+  if (smem_mode >= 1) {
+    V = reinterpret_cast<T*>(eig_smem);
+    W = V + (size_t)M * b;
+    U = W + (size_t)M * b;
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = a.V[o];
+  }
+  if (smem_mode == 2) {
+    T* Cs = U + (size_t)M * b;
+    for (int o = threadIdx.x; o < M * M; o += blockDim.x) Cs[o] = a.C[o];
+    C = Cs;
+  }
   if (threadIdx.x == 0) prev = 1e300;
-  orth_block<T>(a.V, M, b, sh.G);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  orth_block<T>(V, M, b, sh);
   int it = 0;
   bool conv = false;
   for (; it < a.maxit; ++it) {
-    symm_times_block<T>(a.C, a.V, a.W, M, b, b);
+    cv_rows<T>(C, M, V, W, M, b, b, 0, M, warp, kEigWarps);
     __syncthreads();
-    if (rr_step<T>(a.V, a.W, a.U, M, b, r, a.tol, &prev, sh)) {
+    if (rr_step<T>(V, W, U, M, b, r, a.tol, &prev, sh)) {
       conv = true;
       break;
     }
   }
-  symm_times_block<T>(a.C, a.U, a.W, M, b, r);
+  cv_rows<T>(C, M, U, W, M, b, r, 0, M, warp, kEigWarps);
   __syncthreads();
-  final_rr<T>(a.U, a.W, M, b, r, a.Vout, a.theta, sh, H64, Q64, cs64);
+  final_rr<T>(U, W, M, b, r, a.Vout, a.theta, sh, H64, Q64, cs64);
   if (threadIdx.x == 0 && a.stats) {
     atomicAdd(&a.stats[0], 1ull);
     atomicAdd(&a.stats[1], (unsigned long long)(it + (conv ? 1 : 0)));
@@ -471,35 +565,14 @@ __global__ void __launch_bounds__(kEigThreads) eig_begin_kernel(EigArgs<T> a) {
     a.ctl->it = 0;
     a.ctl->prev_worst = 1e300;
   }
-  orth_block<T>(a.V, a.M, a.b, sh.G);
+  orth_block<T>(a.V, a.M, a.b, sh);
 }
 
-// W[:, :ncols] = C V[:, :ncols]; one warp per row of C, lanes over columns of
-// C (coalesced), b partial sums per lane reduced by shuffles.
 template <typename T>
 __global__ void __launch_bounds__(256) symm_mul_kernel(EigArgs<T> a, const T* V, T* W, int ncols, int respect_done) {
   if (respect_done && a.ctl->done) return;
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= a.M) return;
-  const T* crow = a.C + (size_t)row * a.M;
-  T s[kBMax];
-#pragma unroll
-  for (int j = 0; j < kBMax; ++j) s[j] = T(0);
-  for (int k = lane; k < a.M; k += 32) {
-    const T c = crow[k];
-    const T* vr = V + (size_t)k * a.b;
-#pragma unroll
-    for (int j = 0; j < kBMax; ++j)
-      if (j < ncols) s[j] += c * vr[j];
-  }
-#pragma unroll
-  for (int j = 0; j < kBMax; ++j) {
-    if (j < ncols) {
-      const T v = warp_sum(s[j]);
-      if (lane == 0) W[(size_t)row * a.b + j] = v;
-    }
-  }
+  const int row0 = blockIdx.x * 8;
+  cv_rows<T>(a.C, a.M, V, W, a.M, a.b, ncols, row0, min(a.M, row0 + 8), threadIdx.x >> 5, 8);
 }
 
 template <typename T>
@@ -740,7 +813,15 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
   a.ctl = static_cast<EigCtl*>(e.ctl);
   a.stats = e.stats;
   if (e.M <= kEigSmallMax) {
-    eig_kernel<T><<<1, kEigThreads, 0, st>>>(a);
+    cudaFuncAttributes fa;
+    MACH_CUDA_TRY(cudaFuncGetAttributes(&fa, eig_kernel<T>));
+    int dev = 0, optin = 0;
+    MACH_CUDA_TRY(cudaGetDevice(&dev));
+    MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t budget = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
+    const EigSmemPlan plan = eig_smem_plan(e.M, e.b, sizeof(T), budget);
+    MACH_CUDA_TRY(cudaFuncSetAttribute(eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.bytes));
+    eig_kernel<T><<<1, kEigThreads, plan.bytes, st>>>(a, plan.mode);
     MACH_LAUNCH_CHECK();
     return MACH_OK;
   }

@@ -93,8 +93,10 @@ def tucker_torch(spec: TuckerSpec, device="cuda", chunk_elems: int = 1 << 27):
         G = G * torch.where(torch.rand(ranks, generator=gen, device=device, dtype=torch.float64) < 0.5, -1.0, 1.0)
     Us = []
     for n, r in zip(spec.dims, ranks):
-        q, _ = torch.linalg.qr(torch.randn(n, r, generator=gen, device=device, dtype=torch.float64))
-        Us.append(q)
+        # small QR on the host (keeps the device generator free of solver libraries)
+        g = torch.randn(n, r, generator=gen, device=device, dtype=torch.float64).cpu().numpy()
+        q, _ = np.linalg.qr(g)
+        Us.append(torch.from_numpy(np.ascontiguousarray(q)).to(device))
     d = len(spec.dims)
     letters = "abcdefgh"
     upper = "ABCDEFGH"
