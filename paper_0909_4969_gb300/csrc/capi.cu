@@ -613,6 +613,8 @@ mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cu
   L.A_mid0 = d >= 3 ? w.fac[c.mid[0]].ptr : nullptr;
   L.A_mid1 = d >= 4 ? w.fac[c.mid[1]].ptr : nullptr;
   L.I_leaf = (int)h->dims[c.leaf];
+  L.I_mid0 = d >= 3 ? (int)h->dims[c.mid[0]] : 0;
+  L.I_mid1 = d >= 4 ? (int)h->dims[c.mid[1]] : 0;
   L.r_leaf = ranks[c.leaf];
   L.r_mid0 = d >= 3 ? ranks[c.mid[0]] : 1;
   L.r_mid1 = d >= 4 ? ranks[c.mid[1]] : 1;

@@ -118,6 +118,7 @@ __device__ void jacobi_warp(T* H, T* Qm, int n, int ld, int max_sweeps, T rel_to
   __syncwarp();
   if (n <= 1) return;
   const int np = (n + 1) & ~1;  // even number of players (a dummy when n is odd)
+  T prev_off = T(-1);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = T(0), dia = T(0);
     for (int i = lane; i < n; i += 32) {
@@ -128,7 +129,13 @@ __device__ void jacobi_warp(T* H, T* Qm, int n, int ld, int max_sweeps, T rel_to
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
+    // converged, or stalled at the arithmetic's rounding floor (Jacobi
+    // converges quadratically, so a sweep that does not cut the off-diagonal
+    // mass by 4x has reached the floor)
     if (off <= rel_tol * rel_tol * dia) break;
+    const T floor_rel = sizeof(T) == 8 ? T(1e-12) : T(1e-4);
+    if (prev_off >= T(0) && off > T(0.25) * prev_off && off <= floor_rel * floor_rel * dia) break;
+    prev_off = off;
     for (int round = 0; round < np - 1; ++round) {
       if (lane < np / 2) {
         const int pa = lane, pb = np - 1 - lane;
@@ -399,7 +406,7 @@ __device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, doubl
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    jacobi_warp<T>(sh.H, sh.Qm, b, kBMax, 30, sizeof(T) == 8 ? T(1e-15) : T(1e-7), sh.cs, sh.pq);
+    jacobi_warp<T>(sh.H, sh.Qm, b, kBMax, 20, sizeof(T) == 8 ? T(1e-15) : T(1e-7), sh.cs, sh.pq);
     sort_desc_warp<T>(sh.H, b, kBMax, sh.perm);
   }
   __syncthreads();

@@ -294,7 +294,7 @@ struct TtmcLaunch {
   const void* A_leaf;
   const void* A_mid0;
   const void* A_mid1;
-  int I_leaf;
+  int I_leaf, I_mid0, I_mid1;
   int r_leaf, r_mid0, r_mid1;
   int J;
   void* Y;

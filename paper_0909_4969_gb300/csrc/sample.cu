@@ -3,17 +3,18 @@
 // whether the entry is kept; kept (l, value) pairs are compacted in increasing
 // l.  The coin is value-independent, so the dense input is streamed once.
 //
-// GB300 design: persistent CTAs claim 32 KiB tiles of X through one atomic
-// counter and stream them into a 3-stage shared-memory ring with 1-D TMA bulk
-// copies completed on mbarriers.  Because the coin does not depend on the
-// data, a CTA evaluates Philox for a tile as soon as it claims it ("count
-// ahead"): each thread covers 8 (FP32) or 4 (FP64) consecutive Philox
-// counters, i.e. 32 / 16 consecutive entries; the keep masks and per-thread
-// prefixes are cached in shared memory and the tile's aggregate is published
-// at once.  When the tile's data has landed, the tile's global offset comes
-// from a decoupled look-back over the published per-tile status words
-// (bounded spin-waits) and the kept (l, value) pairs are written in order.
-// Philox is evaluated exactly once per counter.
+// GB300 design: persistent CTAs (4 per SM) claim 16 KiB tiles of X through
+// one atomic counter and stream them into a 3-stage shared-memory ring with
+// 1-D TMA bulk copies completed on mbarriers.  Because the coin does not
+// depend on the data, a CTA settles a tile's place in the output as soon as
+// it claims it, while the tile's bytes are still in flight: each thread
+// evaluates Philox for 4 (FP32) or 2 (FP64) consecutive counters, i.e. 16 / 8
+// consecutive entries; the keep masks and per-thread prefixes are cached in
+// shared memory; the tile's aggregate is published and its exclusive prefix
+// is found by a decoupled look-back over the per-tile status words (bounded
+// spin-waits), which only walks over tiles claimed just before.  When the
+// data has landed, the kept (l, value) pairs are written in order.  Philox is
+// evaluated exactly once per counter.
 #include "mach_internal.cuh"
 
 namespace mach {
@@ -29,7 +30,7 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
 template <typename V>
 struct SampCfg {
-  static constexpr int kCPT = sizeof(V) == 4 ? 8 : 4;     // Philox counters per thread
+  static constexpr int kCPT = sizeof(V) == 4 ? 4 : 2;     // Philox counters per thread
   static constexpr int kEPT = 4 * kCPT;                      // entries per thread
   static constexpr int kTile = kSampThreads * kEPT;          // entries per tile
   static constexpr size_t kStageBytes = (size_t)kTile * sizeof(V);
@@ -91,9 +92,8 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
   __shared__ long long stage_tile[kSampStages];
   __shared__ uint32_t s_mask[kSampStages][kSampThreads];
   __shared__ int s_pre[kSampStages][kSampThreads];   // per-thread exclusive prefix in the tile
-  __shared__ int s_agg[kSampStages];
+  __shared__ long long s_excl[kSampStages];
   __shared__ int warp_tot[kSampWarps];
-  __shared__ long long s_excl;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
   };
 
   // All threads: evaluate the coin for the tile claimed into stage s, cache
-  // masks and prefixes, publish the aggregate (or, for tile 0, the prefix).
-  // Must be called after a __syncthreads that made stage_tile[s] visible.
+  // masks and prefixes, publish the aggregate, look back for the exclusive
+  // prefix and publish the inclusive one.  Must be called after a
+  // __syncthreads that made stage_tile[s] visible.
   auto count_ahead = [&](int s) {
     const long long t = stage_tile[s];
     if (t >= a.num_tiles) return;  // uniform
@@ -168,17 +169,28 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
     }
     s_mask[s][tid] = mask;
     s_pre[s][tid] = warp_off + incl - cnt;
-    if (tid == 0) {
-      s_agg[s] = blk;
-      st_release_u64(&a.tile_status[t], (t == 0 ? kFlagPre : kFlagAgg) | (unsigned long long)blk);
+    if (warp == 0) {
+      long long e = 0;
+      if (t == 0) {
+        if (lane == 0) st_release_u64(&a.tile_status[0], kFlagPre | (unsigned long long)blk);
+      } else {
+        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagAgg | (unsigned long long)blk);
+        e = lookback(a, t, lane);
+        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagPre | (unsigned long long)(e + blk));
+      }
+      if (lane == 0) {
+        s_excl[s] = e;
+        if (t == a.num_tiles - 1) *a.out_count = e + blk;
+      }
     }
-    __syncthreads();  // warp_tot reuse
+    __syncthreads();  // warp_tot reuse, s_excl visible
   };
 
-  if (tid == 0)
-    for (int s = 0; s < kSampStages; ++s) issue(s);
-  __syncthreads();
-  for (int s = 0; s < kSampStages; ++s) count_ahead(s);
+  for (int s = 0; s < kSampStages; ++s) {
+    if (tid == 0) issue(s);
+    __syncthreads();
+    count_ahead(s);
+  }
 
   uint32_t parity = 0;
   int s = 0;
@@ -196,22 +208,13 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
     const long long t = stage_tile[s];
     if (t >= a.num_tiles) break;
 
-    if (warp == 0) {
-      long long e = 0;
-      if (t > 0) {
-        e = lookback(a, t, lane);
-        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagPre | (unsigned long long)(e + s_agg[s]));
-      }
-      if (lane == 0) s_excl = e;
-    }
-    __syncthreads();
     const V* buf = stage_buf + (size_t)s * C::kTile;
     const int64_t e_tile = (int64_t)t * C::kTile;
     const int64_t tile_n = min((int64_t)C::kTile, a.n - e_tile);
     const int64_t n_staged = (int64_t)((((uint64_t)tile_n * sizeof(V)) & ~(uint64_t)15) / sizeof(V));
     const int64_t e_thr = e_tile + (int64_t)tid * C::kEPT;
     uint32_t mask = s_mask[s][tid];
-    long long pos = s_excl + s_pre[s][tid];
+    long long pos = s_excl[s] + s_pre[s][tid];
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -226,7 +229,6 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
       }
       ++pos;
     }
-    if (t == a.num_tiles - 1 && tid == 0) *a.out_count = s_excl + s_agg[s];
     __syncthreads();
     if (tid == 0) issue(s);
     __syncthreads();

@@ -27,11 +27,13 @@ namespace mach {
 
 namespace {
 
-constexpr int kTtmcWarps = 8;
-constexpr int kTtmcThreads = 32 * kTtmcWarps;
+// warps per CTA: 16 for FP32 arithmetic, 8 for FP64 (register budget)
+template <typename T>
+struct TtmcWarps {
+  static constexpr int value = sizeof(T) == 4 ? 16 : 8;
+};
 constexpr int kSQ = 8;                 // level-2 accumulators per lane (d = 4)
-constexpr uint32_t kTaskMax = 2048;    // entries per task (shared-memory staging)
-constexpr uint32_t kLeafStageMax = 16 * 1024;
+constexpr uint32_t kTaskMax = 1024;    // entries per task (shared-memory staging)
 
 template <typename T>
 struct TtmcArgs {
@@ -49,7 +51,9 @@ struct TtmcArgs {
   int r_leaf, r_mid0, r_mid1;
   int J;                      // row length of Y
   int Q;                      // level-2 width: d == 4: r_mid1 * r_leaf, else J
-  uint32_t leaf_bytes_staged; // 0 = read A_leaf through L1
+  uint32_t leaf_bytes_staged; // bytes of each factor copied to shared memory
+  uint32_t mid0_bytes_staged; // (0 = read it through L1)
+  uint32_t mid1_bytes_staged;
   T* Y;                       // I_n x J
   T* partial;                 // ntask x J
   unsigned* err;
@@ -64,38 +68,49 @@ struct WarpStage {
 };
 
 template <typename V, typename T, int D, int ACC, int RLM>
-__global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
+__global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs<T> a) {
+  constexpr int kW = TtmcWarps<T>::value;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bar_leaf;
-  __shared__ uint64_t bar_warp[kTtmcWarps];
-  __shared__ T sz[kTtmcWarps][32][RLM + 1];
-  __shared__ uint32_t smid[kTtmcWarps][32];
+  __shared__ uint64_t bar_fac;
+  __shared__ uint64_t bar_warp[kW];
+  __shared__ T sz[kW][32][RLM + 1];
+  __shared__ uint32_t smid[kW][32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const V* val = static_cast<const V*>(a.val);
-  unsigned char* wbuf = smem_raw + a.leaf_bytes_staged + (size_t)warp * WarpStage<V>::kBytes;
+  const uint32_t fac_bytes = a.leaf_bytes_staged + a.mid0_bytes_staged + a.mid1_bytes_staged;
+  unsigned char* wbuf = smem_raw + fac_bytes + (size_t)warp * WarpStage<V>::kBytes;
   V* sval = reinterpret_cast<V*>(wbuf);
   uint16_t* sleaf = reinterpret_cast<uint16_t*>(wbuf + WarpStage<V>::kValBytes);
 
   if (tid == 0) {
-    mbar_init(&bar_leaf, 1);
-    for (int w = 0; w < kTtmcWarps; ++w) mbar_init(&bar_warp[w], 1);
+    mbar_init(&bar_fac, 1);
+    for (int w = 0; w < kW; ++w) mbar_init(&bar_warp[w], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  // Stage the leaf factor (the hottest gather) in shared memory when small.
+  // Stage the factor matrices (gathered per entry and per fibre) in shared
+  // memory with TMA bulk copies, as far as they fit.
   const T* Aleaf = a.A_leaf;
-  if (a.leaf_bytes_staged) {
-    T* sA = reinterpret_cast<T*>(smem_raw);
+  const T* Amid0 = a.A_mid0;
+  const T* Amid1 = a.A_mid1;
+  if (fac_bytes) {
+    T* sLeaf = reinterpret_cast<T*>(smem_raw);
+    T* sMid0 = reinterpret_cast<T*>(smem_raw + a.leaf_bytes_staged);
+    T* sMid1 = reinterpret_cast<T*>(smem_raw + a.leaf_bytes_staged + a.mid0_bytes_staged);
     if (tid == 0) {
-      mbar_arrive_expect_tx(&bar_leaf, a.leaf_bytes_staged);
-      bulk_g2s(sA, a.A_leaf, a.leaf_bytes_staged, &bar_leaf);
+      mbar_arrive_expect_tx(&bar_fac, fac_bytes);
+      if (a.leaf_bytes_staged) bulk_g2s(sLeaf, a.A_leaf, a.leaf_bytes_staged, &bar_fac);
+      if (a.mid0_bytes_staged) bulk_g2s(sMid0, a.A_mid0, a.mid0_bytes_staged, &bar_fac);
+      if (a.mid1_bytes_staged) bulk_g2s(sMid1, a.A_mid1, a.mid1_bytes_staged, &bar_fac);
     }
-    if (!mbar_wait_bounded(&bar_leaf, 0)) {
+    if (!mbar_wait_bounded(&bar_fac, 0)) {
       if (tid == 0) atomicOr(a.err, DEV_TIMEOUT);
       return;
     }
-    Aleaf = sA;
+    if (a.leaf_bytes_staged) Aleaf = sLeaf;
+    if (a.mid0_bytes_staged) Amid0 = sMid0;
+    if (a.mid1_bytes_staged) Amid1 = sMid1;
   }
 
   const int rl = a.r_leaf;
@@ -112,8 +127,8 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
 
   const uint32_t ntask = *a.d_ntask;
   const uint32_t nfib = *a.d_nfib;
-  const int gwarp = blockIdx.x * kTtmcWarps + warp;
-  const int nwarps = gridDim.x * kTtmcWarps;
+  const int gwarp = blockIdx.x * kW + warp;
+  const int nwarps = gridDim.x * kW;
   uint32_t phase = 0;
 
   for (uint32_t t = gwarp; t < ntask; t += nwarps) {
@@ -141,7 +156,7 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
 
     auto flush_w = [&]() {
       if (D == 4 && cur_a1 != 0xffffffffu) {
-        const T* arow = a.A_mid0 + (size_t)cur_a1 * a.r_mid0;
+        const T* arow = Amid0 + (size_t)cur_a1 * a.r_mid0;
 #pragma unroll
         for (int r1 = 0; r1 < kMaxRank; ++r1) {
           if (r1 < a.r_mid0) {
@@ -199,7 +214,7 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
         if (D == 2) {
           if (lane < rl) acc[0] += zj[lane];
         } else if (D == 3) {
-          const T* arow = a.A_mid0 + (size_t)smid[warp][j] * a.r_mid0;
+          const T* arow = Amid0 + (size_t)smid[warp][j] * a.r_mid0;
 #pragma unroll
           for (int s = 0; s < ACC; ++s)
             if (lane + 32 * s < Q) acc[s] += arow[qa[s]] * zj[qb[s]];
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(kTtmcThreads) ttmc_kernel(TtmcArgs<T> a) {
             flush_w();
             cur_a1 = a1;
           }
-          const T* arow = a.A_mid1 + (size_t)a2 * a.r_mid1;
+          const T* arow = Amid1 + (size_t)a2 * a.r_mid1;
 #pragma unroll
           for (int s = 0; s < kSQ; ++s)
             if (s < SQ && lane + 32 * s < Q) w[s] += arow[qa[s]] * zj[qb[s]];
@@ -283,21 +298,36 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   a.Y = static_cast<T*>(L.Y);
   a.partial = static_cast<T*>(L.partial);
   a.err = L.err;
-  const size_t leaf_bytes = (size_t)L.I_leaf * L.r_leaf * sizeof(T);
-  const size_t staged = (leaf_bytes + 15) & ~(size_t)15;
-  a.leaf_bytes_staged = staged <= kLeafStageMax ? (uint32_t)staged : 0u;
-  const size_t smem = a.leaf_bytes_staged + (size_t)kTtmcWarps * WarpStage<V>::kBytes;
-  MACH_CUDA_TRY(cudaFuncSetAttribute(ttmc_kernel<V, T, D, ACC, RLM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+  constexpr int kW = TtmcWarps<T>::value;
+  auto kern = ttmc_kernel<V, T, D, ACC, RLM>;
+  cudaFuncAttributes fa;
+  MACH_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, optin = 0;
+  MACH_CUDA_TRY(cudaGetDevice(&dev));
+  MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t warp_bytes = (size_t)kW * WarpStage<V>::kBytes;
+  size_t budget = (size_t)optin > fa.sharedSizeBytes + warp_bytes + 1024
+                      ? (size_t)optin - fa.sharedSizeBytes - warp_bytes - 1024 : 0;
+  // greedy: leaf factor (gathered per entry) first, then the mid factors
+  auto take = [&](size_t elems) -> uint32_t {
+    const size_t by = (elems * sizeof(T) + 15) & ~(size_t)15;
+    if (elems == 0 || by > budget) return 0u;
+    budget -= by;
+    return (uint32_t)by;
+  };
+  a.leaf_bytes_staged = take((size_t)L.I_leaf * L.r_leaf);
+  a.mid0_bytes_staged = D >= 3 ? take((size_t)L.I_mid0 * L.r_mid0) : 0u;
+  a.mid1_bytes_staged = D >= 4 ? take((size_t)L.I_mid1 * L.r_mid1) : 0u;
+  const size_t smem = (size_t)a.leaf_bytes_staged + a.mid0_bytes_staged + a.mid1_bytes_staged + warp_bytes;
+  MACH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttmc_kernel<V, T, D, ACC, RLM>,
-                                                              kTtmcThreads, smem));
+  MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kW, smem));
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms() * per_sm;
-  const int64_t need = ceil_div(L.ntask_cap, kTtmcWarps);
+  const int64_t need = ceil_div(L.ntask_cap, kW);
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  ttmc_kernel<V, T, D, ACC, RLM><<<(unsigned)grid, kTtmcThreads, smem, st>>>(a);
+  kern<<<(unsigned)grid, 32 * kW, smem, st>>>(a);
   MACH_LAUNCH_CHECK();
   ttmc_fixup_kernel<T><<<L.nrows, 128, 0, st>>>(L.row_task, L.J, static_cast<const T*>(L.partial),
                                                  static_cast<T*>(L.Y));
