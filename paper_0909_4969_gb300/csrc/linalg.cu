@@ -104,41 +104,56 @@ __global__ void init_gram_kernel(const V* __restrict__ val, const uint16_t* __re
 
 // ----------------------------------------------------------------------------
 // Cyclic Jacobi for a small symmetric matrix (n <= 32) held in shared memory
-// (row-major, leading dimension ld), one warp.  On return H is (nearly)
-// diagonal and Qm holds the eigenvectors in its columns.
+// (row-major, leading dimension ld), all threads of the CTA.  On return H is
+// (nearly) diagonal and Qm holds the eigenvectors in its columns.
 // Rotation (Golub & Van Loan, sym.schur2): tau = (h_qq - h_pp) / (2 h_pq),
 // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c;
-// H <- J^T H J with J_pp = J_qq = c, J_pq = s, J_qp = -s.
-// ----------------------------------------------------------------------------
+// H <- J^T H J with J_pp = J_qq = c, J_pq = s, J_qp = -s.  Each round applies
+// n/2 disjoint rotations (round-robin ordering); every element of the column
+// and row updates belongs to exactly one thread.  Sweeps stop at the relative
+// off-diagonal tolerance, or at the rounding floor (quadratic convergence: a
+// sweep that no longer cuts the off-diagonal mass 4x near the floor).
 template <typename T>
-__device__ void jacobi_warp(T* H, T* Qm, int n, int ld, int max_sweeps, T rel_tol, T* cs, int* pq) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < n; i += 32)
-    for (int j = 0; j < n; ++j) Qm[i * ld + j] = (i == j) ? T(1) : T(0);
-  __syncwarp();
+__device__ void jacobi_block(T* H, T* Qm, int n, int ld, int max_sweeps, T rel_tol, T* cs, int* pq, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - (e / n) * n;
+    Qm[i * ld + j] = (i == j) ? T(1) : T(0);
+  }
+  __syncthreads();
   if (n <= 1) return;
   const int np = (n + 1) & ~1;  // even number of players (a dummy when n is odd)
-  T prev_off = T(-1);
+  const int npairs = np / 2;
+  double prev_off = -1.0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    T off = T(0), dia = T(0);
-    for (int i = lane; i < n; i += 32) {
-      for (int j = 0; j < n; ++j) {
-        const T h = H[i * ld + j];
-        if (i == j) dia += h * h; else off += h * h;
-      }
+    double off = 0.0, dia = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e - (e / n) * n;
+      const double h = (double)H[i * ld + j];
+      if (i == j) dia += h * h; else off += h * h;
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
-    // converged, or stalled at the arithmetic's rounding floor (Jacobi
-    // converges quadratically, so a sweep that does not cut the off-diagonal
-    // mass by 4x has reached the floor)
-    if (off <= rel_tol * rel_tol * dia) break;
-    const T floor_rel = sizeof(T) == 8 ? T(1e-12) : T(1e-4);
-    if (prev_off >= T(0) && off > T(0.25) * prev_off && off <= floor_rel * floor_rel * dia) break;
+    if (lane == 0) {
+      red[2 * warp] = off;
+      red[2 * warp + 1] = dia;
+    }
+    __syncthreads();
+    off = 0.0;
+    dia = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      off += red[2 * w];
+      dia += red[2 * w + 1];
+    }
+    __syncthreads();
+    if (off <= (double)rel_tol * (double)rel_tol * dia) break;
+    const double floor_rel = sizeof(T) == 8 ? 1e-12 : 1e-4;
+    if (prev_off >= 0.0 && off > 0.25 * prev_off && off <= floor_rel * floor_rel * dia) break;
     prev_off = off;
     for (int round = 0; round < np - 1; ++round) {
-      if (lane < np / 2) {
-        const int pa = lane, pb = np - 1 - lane;
+      if (tid < npairs) {
+        const int pa = tid, pb = np - 1 - tid;
         int p = pa == 0 ? 0 : ((pa - 1 + round) % (np - 1)) + 1;
         int q = pb == 0 ? 0 : ((pb - 1 + round) % (np - 1)) + 1;
         if (p > q) {
@@ -150,48 +165,46 @@ __device__ void jacobi_warp(T* H, T* Qm, int n, int ld, int max_sweeps, T rel_to
         if (q < n) {
           const T hpq = H[p * ld + q];
           const T hpp = H[p * ld + p], hqq = H[q * ld + q];
-          if (hpq != T(0) && fabs((double)hpq) > 1e-300) {
+          if (hpq != T(0)) {
             const T tau = (hqq - hpp) / (T(2) * hpq);
             const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
             c = T(1) / sqrt(T(1) + t * t);
             s = t * c;
           }
         }
-        cs[2 * lane] = c;
-        cs[2 * lane + 1] = s;
-        pq[2 * lane] = p;
-        pq[2 * lane + 1] = q < n ? q : -1;
+        cs[2 * tid] = c;
+        cs[2 * tid + 1] = s;
+        pq[2 * tid] = p;
+        pq[2 * tid + 1] = q < n ? q : -1;
       }
-      __syncwarp();
-      // H <- H J (column rotations), lane owns rows
-      for (int i = lane; i < n; i += 32) {
-        for (int k = 0; k < np / 2; ++k) {
-          const int q = pq[2 * k + 1];
-          if (q < 0) continue;
-          const int p = pq[2 * k];
-          const T c = cs[2 * k], s = cs[2 * k + 1];
-          const T hp = H[i * ld + p], hq = H[i * ld + q];
-          H[i * ld + p] = c * hp - s * hq;
-          H[i * ld + q] = s * hp + c * hq;
-          const T qp = Qm[i * ld + p], qq = Qm[i * ld + q];
-          Qm[i * ld + p] = c * qp - s * qq;
-          Qm[i * ld + q] = s * qp + c * qq;
-        }
+      __syncthreads();
+      // H <- H J and Qm <- Qm J (column rotations): element (i, pair k)
+      for (int e = tid; e < npairs * n; e += nt) {
+        const int k = e / n, i = e - (e / n) * n;
+        const int q = pq[2 * k + 1];
+        if (q < 0) continue;
+        const int p = pq[2 * k];
+        const T c = cs[2 * k], s = cs[2 * k + 1];
+        const T hp = H[i * ld + p], hq = H[i * ld + q];
+        H[i * ld + p] = c * hp - s * hq;
+        H[i * ld + q] = s * hp + c * hq;
+        const T qp = Qm[i * ld + p], qq = Qm[i * ld + q];
+        Qm[i * ld + p] = c * qp - s * qq;
+        Qm[i * ld + q] = s * qp + c * qq;
       }
-      __syncwarp();
-      // H <- J^T H (row rotations), lane owns columns
-      for (int j = lane; j < n; j += 32) {
-        for (int k = 0; k < np / 2; ++k) {
-          const int q = pq[2 * k + 1];
-          if (q < 0) continue;
-          const int p = pq[2 * k];
-          const T c = cs[2 * k], s = cs[2 * k + 1];
-          const T hp = H[p * ld + j], hq = H[q * ld + j];
-          H[p * ld + j] = c * hp - s * hq;
-          H[q * ld + j] = s * hp + c * hq;
-        }
+      __syncthreads();
+      // H <- J^T H (row rotations): element (pair k, j)
+      for (int e = tid; e < npairs * n; e += nt) {
+        const int k = e / n, j = e - (e / n) * n;
+        const int q = pq[2 * k + 1];
+        if (q < 0) continue;
+        const int p = pq[2 * k];
+        const T c = cs[2 * k], s = cs[2 * k + 1];
+        const T hp = H[p * ld + j], hq = H[q * ld + j];
+        H[p * ld + j] = c * hp - s * hq;
+        H[q * ld + j] = s * hp + c * hq;
       }
-      __syncwarp();
+      __syncthreads();
     }
   }
 }
@@ -405,10 +418,8 @@ __device__ bool rr_step(T* V, T* W, T* U, int M, int b, int r, double tol, doubl
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    jacobi_warp<T>(sh.H, sh.Qm, b, kBMax, 20, sizeof(T) == 8 ? T(1e-15) : T(1e-7), sh.cs, sh.pq);
-    sort_desc_warp<T>(sh.H, b, kBMax, sh.perm);
-  }
+  jacobi_block<T>(sh.H, sh.Qm, b, kBMax, 20, sizeof(T) == 8 ? T(1e-15) : T(1e-7), sh.cs, sh.pq, sh.red);
+  if (threadIdx.x < 32) sort_desc_warp<T>(sh.H, b, kBMax, sh.perm);
   __syncthreads();
   double loc[kBMax];
   for (int j = 0; j < kBMax; ++j) loc[j] = 0.0;
@@ -467,10 +478,8 @@ __device__ void final_rr(const T* U, const T* W, int M, int b, int r, double* Vo
     H64[q * kBMax + p] = s;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    jacobi_warp<double>(H64, Q64, r, kBMax, 30, 1e-15, cs64, sh.pq);
-    sort_desc_warp<double>(H64, r, kBMax, sh.perm);
-  }
+  jacobi_block<double>(H64, Q64, r, kBMax, 30, 1e-15, cs64, sh.pq, sh.red);
+  if (threadIdx.x < 32) sort_desc_warp<double>(H64, r, kBMax, sh.perm);
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     double ur[kMaxRank];
