@@ -33,7 +33,7 @@ struct TtmcWarps {
   static constexpr int value = sizeof(T) == 4 ? 16 : 8;
 };
 constexpr int kSQ = 8;                 // level-2 accumulators per lane (d = 4)
-constexpr uint32_t kTaskMax = 1024;    // entries per task (shared-memory staging)
+constexpr uint32_t kTaskMax = 512;     // entries per task (shared-memory staging, double-buffered)
 
 template <typename T>
 struct TtmcArgs {
@@ -72,20 +72,21 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
   constexpr int kW = TtmcWarps<T>::value;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bar_fac;
-  __shared__ uint64_t bar_warp[kW];
+  __shared__ uint64_t bar_warp[kW][2];
   __shared__ T sz[kW][32][RLM + 1];
   __shared__ uint32_t smid[kW][32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const V* val = static_cast<const V*>(a.val);
   const uint32_t fac_bytes = a.leaf_bytes_staged + a.mid0_bytes_staged + a.mid1_bytes_staged;
-  unsigned char* wbuf = smem_raw + fac_bytes + (size_t)warp * WarpStage<V>::kBytes;
-  V* sval = reinterpret_cast<V*>(wbuf);
-  uint16_t* sleaf = reinterpret_cast<uint16_t*>(wbuf + WarpStage<V>::kValBytes);
+  unsigned char* wbuf0 = smem_raw + fac_bytes + (size_t)warp * 2 * WarpStage<V>::kBytes;
 
   if (tid == 0) {
     mbar_init(&bar_fac, 1);
-    for (int w = 0; w < kW; ++w) mbar_init(&bar_warp[w], 1);
+    for (int w = 0; w < kW; ++w) {
+      mbar_init(&bar_warp[w][0], 1);
+      mbar_init(&bar_warp[w][1], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -129,23 +130,37 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
   const uint32_t nfib = *a.d_nfib;
   const int gwarp = blockIdx.x * kW + warp;
   const int nwarps = gridDim.x * kW;
-  uint32_t phase = 0;
+  uint32_t phase_bits = 0;
+  // entries [e0, e1) of a task are staged from the 16-byte boundary below e0
+  constexpr uint32_t kAlign = 16 / sizeof(uint16_t);   // 8 entries (also a multiple of 16 B of V)
+  // lane 0: start the bulk copies of task tt into staging buffer `buf`
+  auto stage_task = [&](uint32_t tt, int buf) {
+    if (lane == 0) {
+      const int4 tk = a.tasks[tt];
+      const uint32_t b0 = (uint32_t)tk.y & ~(kAlign - 1);
+      const uint32_t ns = (((uint32_t)tk.z - b0) + kAlign - 1) & ~(kAlign - 1);
+      const uint32_t vb = ns * (uint32_t)sizeof(V), lb = ns * 2u;
+      unsigned char* wb = wbuf0 + (size_t)buf * WarpStage<V>::kBytes;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar_warp[warp][buf], vb + lb);
+      bulk_g2s(wb, val + b0, vb, &bar_warp[warp][buf]);
+      bulk_g2s(wb + WarpStage<V>::kValBytes, a.leaf + b0, lb, &bar_warp[warp][buf]);
+    }
+  };
+  if ((uint32_t)gwarp < ntask) stage_task((uint32_t)gwarp, 0);
+  int cur = 0;
 
-  for (uint32_t t = gwarp; t < ntask; t += nwarps) {
+  for (uint32_t t = gwarp; t < ntask; t += nwarps, cur ^= 1) {
+    // prefetch the next task into the other buffer (freed at the end of the
+    // previous iteration) while this one is processed
+    if (t + nwarps < ntask) stage_task(t + nwarps, cur ^ 1);
     const int4 tk = a.tasks[t];
     const int row = tk.x;
     const uint32_t e0 = (uint32_t)tk.y, e1 = (uint32_t)tk.z;
-    // stage entries [e0, e1): round the start down to a 16-byte boundary of both arrays
-    const uint32_t ealign = 16 / sizeof(uint16_t);   // 8 entries (also a multiple of 16 B of V)
-    const uint32_t base = e0 & ~(ealign - 1);
-    const uint32_t nstage = ((e1 - base) + ealign - 1) & ~(ealign - 1);
-    if (lane == 0) {
-      const uint32_t vb = nstage * (uint32_t)sizeof(V), lb = nstage * 2u;
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bar_warp[warp], vb + lb);
-      bulk_g2s(sval, val + base, vb, &bar_warp[warp]);
-      bulk_g2s(sleaf, a.leaf + base, lb, &bar_warp[warp]);
-    }
+    const uint32_t base = e0 & ~(kAlign - 1);
+    unsigned char* wbuf = wbuf0 + (size_t)cur * WarpStage<V>::kBytes;
+    const V* sval = reinterpret_cast<const V*>(wbuf);
+    const uint16_t* sleaf = reinterpret_cast<const uint16_t*>(wbuf + WarpStage<V>::kValBytes);
     T acc[ACC];
 #pragma unroll
     for (int s = 0; s < ACC; ++s) acc[s] = T(0);
@@ -171,11 +186,13 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
       }
     };
 
-    if (!mbar_wait_bounded(&bar_warp[warp], phase)) {
+    if (!mbar_wait_bounded(&bar_warp[warp][cur], (phase_bits >> cur) & 1u)) {
       if (lane == 0) atomicOr(a.err, DEV_TIMEOUT);
+      // drain the prefetch of the other buffer (bounded) before leaving
+      if (t + nwarps < ntask) (void)mbar_wait_bounded(&bar_warp[warp][cur ^ 1], (phase_bits >> (cur ^ 1)) & 1u);
       return;
     }
-    phase ^= 1u;
+    phase_bits ^= 1u << cur;
 
     for (uint32_t fb = (uint32_t)tk.w;; fb += 32) {
       const uint32_t f = fb + lane;
@@ -305,7 +322,7 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   int dev = 0, optin = 0;
   MACH_CUDA_TRY(cudaGetDevice(&dev));
   MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t warp_bytes = (size_t)kW * WarpStage<V>::kBytes;
+  const size_t warp_bytes = (size_t)kW * 2 * WarpStage<V>::kBytes;
   size_t budget = (size_t)optin > fa.sharedSizeBytes + warp_bytes + 1024
                       ? (size_t)optin - fa.sharedSizeBytes - warp_bytes - 1024 : 0;
   // greedy: leaf factor (gathered per entry) first, then the mid factors
