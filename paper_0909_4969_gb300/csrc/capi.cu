@@ -639,7 +639,8 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   const int M = jroute ? J : I;
   const int b = block_size_for(M, r, !warm);
   MACH_TRY(launch_start_block<T>(static_cast<const T*>(w.Y.ptr), static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
-                                 jroute, warm, static_cast<T*>(w.V.ptr), 0x1000u + (uint32_t)n, st));
+                                 jroute, warm, static_cast<T*>(w.V.ptr), static_cast<T*>(w.U.ptr),
+                                 0x1000u + (uint32_t)n, st));
   EigLaunch e;
   e.M = M;
   e.r = r;

@@ -634,14 +634,49 @@ __global__ void fill_random_block(T* V, int M, int b, int col0, uint32_t salt) {
   }
 }
 
-// V[:, :r] = Y^T A (Y: I x J row-major, A: I x r row-major T), V: J x b.
+// Partial products for V[:, :r] = Y^T A (Y: I x J row-major, A: I x r
+// row-major T): CTA (jb, sp) handles columns [32 jb, 32 jb + 32) of Y over the
+// rows i = sp, sp + nsplit, ..; threads (tx, ty): tx = column, ty = row
+// phase; coalesced reads of Y rows, A rows broadcast.  Partials land in
+// part[sp][j][k] and are summed in split order by yt_reduce (deterministic).
 template <typename T>
-__global__ void yt_times_a(const T* __restrict__ Y, const T* __restrict__ A, int I, int J, int r, T* V, int b) {
+__global__ void __launch_bounds__(256) yt_times_a_part(const T* __restrict__ Y, const T* __restrict__ A, int I,
+                                                       int J, int r, int nsplit, T* __restrict__ part) {
+  __shared__ T red[8][32][kMaxRank + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + tx;
+  const int sp = blockIdx.y;
+  T acc[kMaxRank];
+#pragma unroll
+  for (int k = 0; k < kMaxRank; ++k) acc[k] = T(0);
+  if (j < J) {
+    for (int i = sp + ty * nsplit; i < I; i += 8 * nsplit) {
+      const T y = Y[(size_t)i * J + j];
+      const T* ar = A + (size_t)i * r;
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k)
+        if (k < r) acc[k] += y * ar[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxRank; ++k) red[ty][tx][k] = acc[k];
+  __syncthreads();
+  if (ty == 0 && j < J) {
+    for (int k = 0; k < r; ++k) {
+      T s = T(0);
+      for (int g = 0; g < 8; ++g) s += red[g][tx][k];
+      part[((size_t)sp * J + j) * r + k] = s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void yt_reduce(const T* __restrict__ part, int nsplit, int J, int r, T* __restrict__ V, int b) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= J * r) return;
   const int j = o / r, k = o - (o / r) * r;
   T s = T(0);
-  for (int i = 0; i < I; ++i) s += Y[(size_t)i * J + j] * A[(size_t)i * r + k];
+  for (int sp = 0; sp < nsplit; ++sp) s += part[(size_t)sp * J * r + o];
   V[(size_t)j * b + k] = s;
 }
 
@@ -859,14 +894,21 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
 
 template <typename T>
 mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
-                               T* V, uint32_t salt, cudaStream_t st) {
+                               T* V, T* scratch, uint32_t salt, cudaStream_t st) {
   const int M = jroute ? J : I;
   fill_random_block<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024)),
                          256, 0, st>>>(V, M, b, warm ? r : 0, salt);
   MACH_LAUNCH_CHECK();
   if (warm) {
     if (jroute) {
-      yt_times_a<T><<<(unsigned)ceil_div((int64_t)J * r, 128), 128, 0, st>>>(Y, Aprev, I, J, r, V, b);
+      // partials (nsplit x J x r) live in `scratch`, which holds J x 32
+      // elements, so nsplit <= 32 / r
+      const int nsplit = std::max(1, std::min(32 / std::max(r, 1), std::max(1, I / 64)));
+      T* part = scratch;
+      yt_times_a_part<T><<<dim3((unsigned)ceil_div(J, 32), (unsigned)nsplit), 256, 0, st>>>(Y, Aprev, I, J, r, nsplit,
+                                                                                           part);
+      MACH_LAUNCH_CHECK();
+      yt_reduce<T><<<(unsigned)ceil_div((int64_t)J * r, 128), 128, 0, st>>>(part, nsplit, J, r, V, b);
     } else {
       copy_cols<T><<<(unsigned)ceil_div((int64_t)I * r, 128), 128, 0, st>>>(Aprev, I, r, V, b);
     }
@@ -910,8 +952,8 @@ mach_status launch_core(const T* Y, const double* A, int I, int J, int r, double
 #define MACH_INST(T)                                                                                             \
   template mach_status launch_gram<T>(const T*, int64_t, int, int64_t, int64_t, T*, T*, int64_t, cudaStream_t);  \
   template mach_status launch_eig<T>(const T*, const EigLaunch&, cudaStream_t);                                  \
-  template mach_status launch_start_block<T>(const T*, const T*, int, int, int, int, bool, bool, T*, uint32_t,   \
-                                             cudaStream_t);                                                      \
+  template mach_status launch_start_block<T>(const T*, const T*, int, int, int, int, bool, bool, T*, T*,       \
+                                             uint32_t, cudaStream_t);                                            \
   template mach_status launch_lsv_finish<T>(const T*, const double*, const double*, int, int, int, bool,         \
                                             double*, double*, unsigned*, double*, unsigned*, double*, T*,        \
                                             cudaStream_t);                                                       \

@@ -325,7 +325,7 @@ template <typename T>
 mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st);
 template <typename T>
 mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
-                               T* V, uint32_t salt, cudaStream_t st);
+                               T* V, T* scratch, uint32_t salt, cudaStream_t st);
 template <typename T>
 mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* theta, int I, int J, int r, bool jroute,
                               double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
