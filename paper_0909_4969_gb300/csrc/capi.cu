@@ -142,6 +142,9 @@ struct Workspace {
   int ranks[kMaxModes] = {0, 0, 0, 0};
   DevBuf fac[kMaxModes];  // T row-major I_k x r_k
   DevBuf Y, partial, C, gram_part, V, W, U, Vout, theta, A64, gram64, rinv;
+  DevBuf basis[kMaxModes];   // per mode: last Ritz block (M x b, T)
+  int basis_M[kMaxModes] = {0, 0, 0, 0};   // its M and b (0 = none)
+  int basis_b[kMaxModes] = {0, 0, 0, 0};
   int64_t partial_cap_elems = 0;
   int64_t gram_part_cap = 0;
 };
@@ -182,6 +185,10 @@ void free_mode(ModeCsf& m, cudaStream_t s, bool keep_idx) {
 
 void free_ws(Workspace& w, cudaStream_t s) {
   for (auto& f : w.fac) dev_free(f, s);
+  for (int k = 0; k < kMaxModes; ++k) {
+    dev_free(w.basis[k], s);
+    w.basis_M[k] = w.basis_b[k] = 0;
+  }
   dev_free(w.Y, s);
   dev_free(w.partial, s);
   dev_free(w.C, s);
@@ -584,6 +591,7 @@ mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
   MACH_TRY(dev_alloc(w.gram64, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
   MACH_TRY(dev_alloc(w.rinv, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.fac[k], (size_t)h->dims[k] * ranks[k] * sizeof(T) + 64, st));
+  for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.basis[k], (size_t)maxM * 32 * sizeof(T), st));
   for (int k = 0; k < d; ++k) w.ranks[k] = ranks[k];
   w.ready = true;
   (void)maxI;
@@ -641,6 +649,15 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   MACH_TRY(launch_start_block<T>(static_cast<const T*>(w.Y.ptr), static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
                                  jroute, warm, static_cast<T*>(w.V.ptr), static_cast<T*>(w.U.ptr),
                                  0x1000u + (uint32_t)n, st));
+  // Columns r..b of the start block: the previous solve's Ritz vectors of the
+  // same Gram shape, when there is one (the next directions after the top r).
+  if (warm && w.basis_M[n] == M && w.basis_b[n] == b && b > r) {
+    MACH_CUDA_TRY(cudaMemcpy2DAsync(static_cast<T*>(w.V.ptr) + r, (size_t)b * sizeof(T),
+                                    static_cast<const T*>(w.basis[n].ptr) + r, (size_t)b * sizeof(T),
+                                    (size_t)(b - r) * sizeof(T), (size_t)M, cudaMemcpyDeviceToDevice, st));
+  }
+  w.basis_M[n] = M;
+  w.basis_b[n] = b;
   EigLaunch e;
   e.M = M;
   e.r = r;
@@ -654,6 +671,7 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.theta = static_cast<double*>(w.theta.ptr);
   e.ctl = h->dscal()->eig_ctl;
   e.stats = h->dscal()->eig_stats;
+  e.basis_out = w.basis[n].ptr;
   MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));
   return launch_lsv_finish<T>(static_cast<const T*>(w.Y.ptr), e.Vout, e.theta, I, J, r, jroute,
                               static_cast<double*>(w.A64.ptr), static_cast<double*>(w.gram64.ptr),

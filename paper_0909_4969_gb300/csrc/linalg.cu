@@ -285,32 +285,38 @@ struct EigArgs {
   double tol;          // relative residual tolerance
   EigCtl* ctl;         // split path only
   unsigned long long* stats;  // [0] calls, [1] iterations, [2] unconverged
+  T* basis_out;        // M x b: the final Ritz block (warm start of the next solve), or null
 };
 
-// W[:, :ncols] = C V[:, :ncols] (row stride b for V and W).  One warp per row
-// of C, lanes over the columns of C; rows [row0, row1) step by `rstep`.
+// W[:, :ncols] = C V[:, :ncols] (row stride b for V and W).  A warp owns 4
+// rows of C at a time, lane j owns column j of V: each step reads one
+// coalesced row of V (shared by the 4 rows) and 4 broadcast entries of C.
+// Rows [row0, row1) are shared among `nwarps` warps.
 template <typename T>
 __device__ void cv_rows(const T* C, int ldc, const T* V, T* W, int M, int b, int ncols, int row0, int row1,
                         int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
-  for (int i = row0 + warp; i < row1; i += nwarps) {
-    const T* crow = C + (size_t)i * ldc;
-    T s[kBMax];
-#pragma unroll
-    for (int j = 0; j < kBMax; ++j) s[j] = T(0);
-    for (int k = lane; k < M; k += 32) {
-      const T c = crow[k];
-      const T* vr = V + (size_t)k * b;
-#pragma unroll
-      for (int j = 0; j < kBMax; ++j)
-        if (j < ncols) s[j] += c * vr[j];
-    }
-#pragma unroll
-    for (int j = 0; j < kBMax; ++j) {
-      if (j < ncols) {
-        const T v = warp_sum(s[j]);
-        if (lane == 0) W[(size_t)i * b + j] = v;
+  for (int i0 = row0 + 4 * warp; i0 < row1; i0 += 4 * nwarps) {
+    const int nr = min(4, row1 - i0);
+    const T* c0 = C + (size_t)i0 * ldc;
+    const T* c1 = c0 + (nr > 1 ? ldc : 0);
+    const T* c2 = c0 + (nr > 2 ? 2 * (size_t)ldc : 0);
+    const T* c3 = c0 + (nr > 3 ? 3 * (size_t)ldc : 0);
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    if (lane < ncols) {
+      const T* vc = V + lane;
+#pragma unroll 4
+      for (int k = 0; k < M; ++k) {
+        const T v = vc[(size_t)k * b];
+        s0 += c0[k] * v;
+        s1 += c1[k] * v;
+        s2 += c2[k] * v;
+        s3 += c3[k] * v;
       }
+      W[(size_t)i0 * b + lane] = s0;
+      if (nr > 1) W[(size_t)(i0 + 1) * b + lane] = s1;
+      if (nr > 2) W[(size_t)(i0 + 2) * b + lane] = s2;
+      if (nr > 3) W[(size_t)(i0 + 3) * b + lane] = s3;
     }
   }
 }
@@ -559,6 +565,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(EigArgs<T> a, int smem
       break;
     }
   }
+  if (a.basis_out)
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) a.basis_out[o] = U[o];
   cv_rows<T>(C, M, U, W, M, b, r, 0, M, warp, kEigWarps);
   __syncthreads();
   final_rr<T>(U, W, M, b, r, a.Vout, a.theta, sh, H64, Q64, cs64);
@@ -587,8 +595,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_begin_kernel(EigArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(256) symm_mul_kernel(EigArgs<T> a, const T* V, T* W, int ncols, int respect_done) {
   if (respect_done && a.ctl->done) return;
-  const int row0 = blockIdx.x * 8;
-  cv_rows<T>(a.C, a.M, V, W, a.M, a.b, ncols, row0, min(a.M, row0 + 8), threadIdx.x >> 5, 8);
+  const int row0 = blockIdx.x * 32;
+  cv_rows<T>(a.C, a.M, V, W, a.M, a.b, ncols, row0, min(a.M, row0 + 32), threadIdx.x >> 5, 8);
 }
 
 template <typename T>
@@ -612,6 +620,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_end_kernel(EigArgs<T> a) {
   __shared__ double H64[kBMax * kBMax];
   __shared__ double Q64[kBMax * kBMax];
   __shared__ double cs64[kBMax * 2];
+  if (a.basis_out)
+    for (int o = threadIdx.x; o < a.M * a.b; o += blockDim.x) a.basis_out[o] = a.U[o];
   final_rr<T>(a.U, a.W, a.M, a.b, a.r, a.Vout, a.theta, sh, H64, Q64, cs64);
   if (threadIdx.x == 0 && a.stats) {
     atomicAdd(&a.stats[0], 1ull);
@@ -863,6 +873,7 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
   a.tol = e.tol;
   a.ctl = static_cast<EigCtl*>(e.ctl);
   a.stats = e.stats;
+  a.basis_out = static_cast<T*>(e.basis_out);
   if (e.M <= kEigSmallMax) {
     cudaFuncAttributes fa;
     MACH_CUDA_TRY(cudaFuncGetAttributes(&fa, eig_kernel<T>));
@@ -876,7 +887,7 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
     MACH_LAUNCH_CHECK();
     return MACH_OK;
   }
-  const unsigned rows = (unsigned)ceil_div(e.M, 8);
+  const unsigned rows = (unsigned)ceil_div(e.M, 32);
   eig_begin_kernel<T><<<1, kEigThreads, 0, st>>>(a);
   MACH_LAUNCH_CHECK();
   for (int it = 0; it < e.maxit; ++it) {

@@ -320,6 +320,7 @@ struct EigLaunch {
   double* theta;
   void* ctl;                   // >= 64 bytes of device scratch (split path)
   unsigned long long* stats;   // device counters: calls, iterations, unconverged
+  void* basis_out;             // M x b T: final Ritz block, or null
 };
 template <typename T>
 mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st);

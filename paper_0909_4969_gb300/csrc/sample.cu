@@ -3,27 +3,29 @@
 // whether the entry is kept; kept (l, value) pairs are compacted in increasing
 // l.  The coin is value-independent, so the dense input is streamed once.
 //
-// GB300 design: persistent CTAs (4 per SM) claim 16 KiB tiles of X through
-// one atomic counter and stream them into a 3-stage shared-memory ring with
-// 1-D TMA bulk copies completed on mbarriers.  Because the coin does not
-// depend on the data, a CTA settles a tile's place in the output as soon as
-// it claims it, while the tile's bytes are still in flight: each thread
-// evaluates Philox for 4 (FP32) or 2 (FP64) consecutive counters, i.e. 16 / 8
-// consecutive entries; the keep masks and per-thread prefixes are cached in
-// shared memory; the tile's aggregate is published and its exclusive prefix
-// is found by a decoupled look-back over the per-tile status words (bounded
-// spin-waits), which only walks over tiles claimed just before.  When the
-// data has landed, the kept (l, value) pairs are written in order.  Philox is
-// evaluated exactly once per counter.
+// GB300 design: a persistent, warp-specialised kernel.  Per CTA one control
+// warp claims 16 KiB tiles of X (one atomic counter, so claim order is tile
+// order), starts their 1-D TMA bulk copies into a 4-stage shared-memory ring
+// and runs the decoupled look-back; eight compute warps evaluate Philox for
+// each claimed tile as soon as it is claimed (16 FP32 / 8 FP64 consecutive
+// entries per thread), scan the keep counts inside the tile, and, once the
+// tile's global offset is known and its bytes have landed, write the kept
+// (l, value) pairs in order.  Stages are handed between the warps with
+// mbarriers.  Compute counts tile j while the control warp looks back for
+// tile j-1 and the writes of tile j-2 proceed; a stage is refilled only
+// after the following tile's look-back, so no warp waits on a look-back.
+// Philox is evaluated exactly once per counter; every wait is bounded.
 #include "mach_internal.cuh"
 
 namespace mach {
 
 namespace {
 
-constexpr int kSampThreads = 256;
-constexpr int kSampWarps = kSampThreads / 32;
-constexpr int kSampStages = 3;
+constexpr int kCompWarps = 8;
+constexpr int kCompThreads = 32 * kCompWarps;
+constexpr int kSampThreads = kCompThreads + 32;   // + control warp
+constexpr int kSampStages = 4;
+constexpr int kLag = 2;                           // compute writes tile j - kLag after counting tile j
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -32,7 +34,7 @@ template <typename V>
 struct SampCfg {
   static constexpr int kCPT = sizeof(V) == 4 ? 4 : 2;     // Philox counters per thread
   static constexpr int kEPT = 4 * kCPT;                      // entries per thread
-  static constexpr int kTile = kSampThreads * kEPT;          // entries per tile
+  static constexpr int kTile = kCompThreads * kEPT;          // entries per tile
   static constexpr size_t kStageBytes = (size_t)kTile * sizeof(V);
 };
 
@@ -52,9 +54,9 @@ struct SampleArgs {
   unsigned* err;
 };
 
-// Exclusive prefix of tile t (warp 0): walk predecessors 32 at a time until
-// an inclusive prefix is met; every wait is bounded.
-__device__ long long lookback(const SampleArgs& a, long long t, int lane) {
+// Exclusive prefix of tile t (one warp): walk predecessors 32 at a time until
+// an inclusive prefix is met; every wait is bounded.  Returns false on timeout.
+__device__ bool lookback(const SampleArgs& a, long long t, int lane, long long* out) {
   unsigned long long* st = a.tile_status;
   long long excl = 0;
   long long base = t - 1;
@@ -63,11 +65,8 @@ __device__ long long lookback(const SampleArgs& a, long long t, int lane) {
     const long long j = base - lane;
     unsigned long long v = j >= 0 ? ld_acquire_u64(&st[j]) : kFlagPre;
     while (__any_sync(0xffffffffu, (v >> 62) == 0)) {
-      if (++spins > kSpinLimit) {
-        if (lane == 0) atomicOr(a.err, DEV_TIMEOUT);
-        return excl;
-      }
-      __nanosleep(32);
+      if (++spins > kSpinLimit) return false;
+      if (spins > 16) __nanosleep(32);
       if ((v >> 62) == 0) v = ld_acquire_u64(&st[j]);
     }
     const unsigned pre = __ballot_sync(0xffffffffu, (v >> 62) == 2);
@@ -80,7 +79,12 @@ __device__ long long lookback(const SampleArgs& a, long long t, int lane) {
     excl += warp_sum(val);
     base -= 32;
   }
-  return excl;
+  *out = excl;
+  return true;
+}
+
+__device__ __forceinline__ void compute_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kCompThreads) : "memory");
 }
 
 template <typename V>
@@ -88,12 +92,15 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
   using C = SampCfg<V>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   V* stage_buf = reinterpret_cast<V*>(smem_raw);
-  __shared__ uint64_t bars[kSampStages];
+  __shared__ uint64_t bar_claimed[kSampStages], bar_full[kSampStages], bar_counted[kSampStages],
+      bar_prefixed[kSampStages], bar_empty[kSampStages];
   __shared__ long long stage_tile[kSampStages];
-  __shared__ uint32_t s_mask[kSampStages][kSampThreads];
-  __shared__ int s_pre[kSampStages][kSampThreads];   // per-thread exclusive prefix in the tile
   __shared__ long long s_excl[kSampStages];
-  __shared__ int warp_tot[kSampWarps];
+  __shared__ int s_agg[kSampStages];
+  __shared__ uint32_t s_mask[kSampStages][kCompThreads];
+  __shared__ int s_pre[kSampStages][kCompThreads];
+  __shared__ int warp_tot[kSampStages][kCompWarps];
+  __shared__ int s_abort;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -102,37 +109,98 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
   V* out_val = static_cast<V*>(a.out_val);
 
   if (tid == 0) {
-    for (int s = 0; s < kSampStages; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < kSampStages; ++s) {
+      mbar_init(&bar_claimed[s], 1);
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_counted[s], kCompWarps);
+      mbar_init(&bar_prefixed[s], 1);
+      mbar_init(&bar_empty[s], kCompWarps);
+    }
+    s_abort = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  // Thread 0: claim the next tile for stage s and start its copy.
-  auto issue = [&](int s) {
-    const long long t = (long long)atomicAdd(a.tile_counter, 1ull);
-    stage_tile[s] = t;
-    uint32_t bytes = 0;
-    if (t < a.num_tiles) {
-      const int64_t e0 = (int64_t)t * C::kTile;
-      const int64_t ne = min((int64_t)C::kTile, a.n - e0);
-      bytes = (uint32_t)(((uint64_t)ne * sizeof(V)) & ~(uint64_t)15);
+  if (warp == kCompWarps) {
+    // ------------------------------- control warp -------------------------------
+    auto claim = [&](int s) {  // lane 0
+      const long long t = (long long)atomicAdd(a.tile_counter, 1ull);
+      stage_tile[s] = t;
+      uint32_t bytes = 0;
+      if (t < a.num_tiles) {
+        const int64_t e0 = (int64_t)t * C::kTile;
+        const int64_t ne = min((int64_t)C::kTile, a.n - e0);
+        bytes = (uint32_t)(((uint64_t)ne * sizeof(V)) & ~(uint64_t)15);
+      }
+      if (bytes) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar_full[s], bytes);
+        bulk_g2s(stage_buf + (size_t)s * C::kTile, x + (int64_t)t * C::kTile, bytes, &bar_full[s]);
+      } else {
+        mbar_arrive(&bar_full[s]);
+      }
+      mbar_arrive(&bar_claimed[s]);
+      return t;
+    };
+    bool fail = false;
+    if (lane == 0)
+      for (int s = 0; s < kSampStages; ++s) claim(s);
+    __syncwarp();
+    for (long long i = 0;; ++i) {
+      const int s = (int)(i % kSampStages);
+      const uint32_t ph = (uint32_t)((i / kSampStages) & 1);
+      if (!mbar_wait_bounded(&bar_counted[s], ph)) {
+        fail = true;
+        break;
+      }
+      const long long t = stage_tile[s];
+      if (t >= a.num_tiles) break;
+      const int agg = s_agg[s];
+      long long e = 0;
+      if (t == 0) {
+        if (lane == 0) st_release_u64(&a.tile_status[0], kFlagPre | (unsigned long long)agg);
+      } else {
+        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagAgg | (unsigned long long)agg);
+        if (!lookback(a, t, lane, &e)) {
+          fail = true;
+          break;
+        }
+        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagPre | (unsigned long long)(e + agg));
+      }
+      if (lane == 0) {
+        s_excl[s] = e;
+        if (t == a.num_tiles - 1) *a.out_count = e + agg;
+        mbar_arrive(&bar_prefixed[s]);
+      }
+      __syncwarp();
+      // refill the previous tile's stage with tile (i - 1) + stages once
+      // compute has written tile i - 1 (after this look-back, so the next
+      // look-back never waits behind a write)
+      if (i >= 1 && lane == 0) {
+        const int sp = (int)((i - 1) % kSampStages);
+        const uint32_t php = (uint32_t)(((i - 1) / kSampStages) & 1);
+        if (!mbar_wait_bounded(&bar_empty[sp], php)) fail = true;
+        else claim(sp);
+      }
+      if (__any_sync(0xffffffffu, fail)) {
+        fail = true;
+        break;
+      }
     }
-    if (bytes) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bars[s], bytes);
-      bulk_g2s(stage_buf + (size_t)s * C::kTile, x + (int64_t)t * C::kTile, bytes, &bars[s]);
-    } else {
-      mbar_arrive(&bars[s]);
+    if (fail && lane == 0) {
+      atomicOr(a.err, DEV_TIMEOUT);
+      atomicExch(&s_abort, 1);
+      // leave no bulk copy in flight: bounded wait on every stage's current phase
+      for (int s = 0; s < kSampStages; ++s) {
+        (void)mbar_wait_bounded(&bar_full[s], 0);
+        (void)mbar_wait_bounded(&bar_full[s], 1);
+      }
     }
-  };
+    return;
+  }
 
-  // All threads: evaluate the coin for the tile claimed into stage s, cache
-  // masks and prefixes, publish the aggregate, look back for the exclusive
-  // prefix and publish the inclusive one.  Must be called after a
-  // __syncthreads that made stage_tile[s] visible.
-  auto count_ahead = [&](int s) {
-    const long long t = stage_tile[s];
-    if (t >= a.num_tiles) return;  // uniform
+  // ------------------------------- compute warps -------------------------------
+  auto count = [&](int s, long long t) {
     const int64_t e_thr = (int64_t)t * C::kTile + (int64_t)tid * C::kEPT;
     const uint64_t q0 = (uint64_t)e_thr >> 2;
     uint32_t mask = 0;
@@ -158,56 +226,27 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
+    if (lane == 31) warp_tot[s][warp] = incl;
+    compute_bar();
     int warp_off = 0, blk = 0;
 #pragma unroll
-    for (int w = 0; w < kSampWarps; ++w) {
-      const int v = warp_tot[w];
+    for (int w = 0; w < kCompWarps; ++w) {
+      const int v = warp_tot[s][w];
       warp_off += (w < warp) ? v : 0;
       blk += v;
     }
     s_mask[s][tid] = mask;
     s_pre[s][tid] = warp_off + incl - cnt;
-    if (warp == 0) {
-      long long e = 0;
-      if (t == 0) {
-        if (lane == 0) st_release_u64(&a.tile_status[0], kFlagPre | (unsigned long long)blk);
-      } else {
-        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagAgg | (unsigned long long)blk);
-        e = lookback(a, t, lane);
-        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagPre | (unsigned long long)(e + blk));
-      }
-      if (lane == 0) {
-        s_excl[s] = e;
-        if (t == a.num_tiles - 1) *a.out_count = e + blk;
-      }
-    }
-    __syncthreads();  // warp_tot reuse, s_excl visible
+    if (tid == 0) s_agg[s] = blk;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bar_counted[s]);
   };
 
-  for (int s = 0; s < kSampStages; ++s) {
-    if (tid == 0) issue(s);
-    __syncthreads();
-    count_ahead(s);
-  }
-
-  uint32_t parity = 0;
-  int s = 0;
-  for (;;) {
-    const bool ok = mbar_wait_bounded(&bars[s], (parity >> s) & 1u);
-    parity ^= 1u << s;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(a.err, DEV_TIMEOUT);
-      for (int k = 1; k < kSampStages; ++k) {
-        const int s2 = (s + k) % kSampStages;
-        (void)mbar_wait_bounded(&bars[s2], (parity >> s2) & 1u);
-      }
-      break;
-    }
+  auto write = [&](long long j) -> bool {
+    const int s = (int)(j % kSampStages);
+    const uint32_t ph = (uint32_t)((j / kSampStages) & 1);
+    if (!mbar_wait_bounded(&bar_prefixed[s], ph) || !mbar_wait_bounded(&bar_full[s], ph)) return false;
     const long long t = stage_tile[s];
-    if (t >= a.num_tiles) break;
-
     const V* buf = stage_buf + (size_t)s * C::kTile;
     const int64_t e_tile = (int64_t)t * C::kTile;
     const int64_t tile_n = min((int64_t)C::kTile, a.n - e_tile);
@@ -229,11 +268,36 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
       }
       ++pos;
     }
-    __syncthreads();
-    if (tid == 0) issue(s);
-    __syncthreads();
-    count_ahead(s);
-    s = (s + 1 == kSampStages) ? 0 : s + 1;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bar_empty[s]);
+    return true;
+  };
+
+  long long i = 0;
+  bool ok = true;
+  for (;; ++i) {
+    const int s = (int)(i % kSampStages);
+    const uint32_t ph = (uint32_t)((i / kSampStages) & 1);
+    if (!mbar_wait_bounded(&bar_claimed[s], ph)) {
+      ok = false;
+      break;
+    }
+    const long long t = stage_tile[s];
+    if (t >= a.num_tiles) {
+      // end marker: let the control warp see it, then drain the last writes
+      if (lane == 0) mbar_arrive(&bar_counted[s]);
+      break;
+    }
+    count(s, t);
+    if (i >= kLag && !write(i - kLag)) {
+      ok = false;
+      break;
+    }
+    if (s_abort) break;
+  }
+  if (ok) {
+    for (long long j = (i >= kLag ? i - kLag : 0); j < i; ++j)
+      if (!write(j)) break;
   }
 }
 
