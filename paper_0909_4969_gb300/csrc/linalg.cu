@@ -288,35 +288,33 @@ struct EigArgs {
   T* basis_out;        // M x b: the final Ritz block (warm start of the next solve), or null
 };
 
-// W[:, :ncols] = C V[:, :ncols] (row stride b for V and W).  A warp owns 4
+// W[:, :ncols] = C V[:, :ncols] (row stride b for V and W).  A warp owns RPW
 // rows of C at a time, lane j owns column j of V: each step reads one
-// coalesced row of V (shared by the 4 rows) and 4 broadcast entries of C.
+// coalesced row of V (shared by the RPW rows) and RPW broadcast entries of C.
 // Rows [row0, row1) are shared among `nwarps` warps.
-template <typename T>
+template <typename T, int RPW = 4>
 __device__ void cv_rows(const T* C, int ldc, const T* V, T* W, int M, int b, int ncols, int row0, int row1,
                         int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
-  for (int i0 = row0 + 4 * warp; i0 < row1; i0 += 4 * nwarps) {
-    const int nr = min(4, row1 - i0);
-    const T* c0 = C + (size_t)i0 * ldc;
-    const T* c1 = c0 + (nr > 1 ? ldc : 0);
-    const T* c2 = c0 + (nr > 2 ? 2 * (size_t)ldc : 0);
-    const T* c3 = c0 + (nr > 3 ? 3 * (size_t)ldc : 0);
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  for (int i0 = row0 + RPW * warp; i0 < row1; i0 += RPW * nwarps) {
+    const int nr = min(RPW, row1 - i0);
+    const T* crow[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) crow[q] = C + (size_t)(i0 + (q < nr ? q : 0)) * ldc;
+    T acc[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) acc[q] = T(0);
     if (lane < ncols) {
       const T* vc = V + lane;
 #pragma unroll 4
       for (int k = 0; k < M; ++k) {
         const T v = vc[(size_t)k * b];
-        s0 += c0[k] * v;
-        s1 += c1[k] * v;
-        s2 += c2[k] * v;
-        s3 += c3[k] * v;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) acc[q] += crow[q][k] * v;
       }
-      W[(size_t)i0 * b + lane] = s0;
-      if (nr > 1) W[(size_t)(i0 + 1) * b + lane] = s1;
-      if (nr > 2) W[(size_t)(i0 + 2) * b + lane] = s2;
-      if (nr > 3) W[(size_t)(i0 + 3) * b + lane] = s3;
+#pragma unroll
+      for (int q = 0; q < RPW; ++q)
+        if (q < nr) W[(size_t)(i0 + q) * b + lane] = acc[q];
     }
   }
 }
@@ -595,8 +593,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_begin_kernel(EigArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(256) symm_mul_kernel(EigArgs<T> a, const T* V, T* W, int ncols, int respect_done) {
   if (respect_done && a.ctl->done) return;
-  const int row0 = blockIdx.x * 32;
-  cv_rows<T>(a.C, a.M, V, W, a.M, a.b, ncols, row0, min(a.M, row0 + 32), threadIdx.x >> 5, 8);
+  const int row0 = blockIdx.x * 8;
+  cv_rows<T, 1>(a.C, a.M, V, W, a.M, a.b, ncols, row0, min(a.M, row0 + 8), threadIdx.x >> 5, 8);
 }
 
 template <typename T>
@@ -887,7 +885,7 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
     MACH_LAUNCH_CHECK();
     return MACH_OK;
   }
-  const unsigned rows = (unsigned)ceil_div(e.M, 32);
+  const unsigned rows = (unsigned)ceil_div(e.M, 8);
   eig_begin_kernel<T><<<1, kEigThreads, 0, st>>>(a);
   MACH_LAUNCH_CHECK();
   for (int it = 0; it < e.maxit; ++it) {

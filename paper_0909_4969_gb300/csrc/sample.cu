@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
       if (t == 0) {
         if (lane == 0) st_release_u64(&a.tile_status[0], kFlagPre | (unsigned long long)agg);
       } else {
-        if (lane == 0) st_release_u64(&a.tile_status[t], kFlagAgg | (unsigned long long)agg);
         if (!lookback(a, t, lane, &e)) {
           fail = true;
           break;
@@ -237,7 +236,11 @@ __global__ void __launch_bounds__(kSampThreads) sample_kernel(SampleArgs a) {
     }
     s_mask[s][tid] = mask;
     s_pre[s][tid] = warp_off + incl - cnt;
-    if (tid == 0) s_agg[s] = blk;
+    if (tid == 0) {
+      s_agg[s] = blk;
+      // publish the aggregate at once (decoupled from this CTA's look-backs)
+      if (t > 0) st_release_u64(&a.tile_status[t], kFlagAgg | (unsigned long long)blk);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&bar_counted[s]);
   };
