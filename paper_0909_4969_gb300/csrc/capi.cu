@@ -142,6 +142,7 @@ struct Workspace {
   int ranks[kMaxModes] = {0, 0, 0, 0};
   DevBuf fac[kMaxModes];  // T row-major I_k x r_k
   DevBuf Y, partial, C, gram_part, V, W, U, Vout, theta, A64, gram64, rinv;
+  DevBuf eig_part;           // split-path partial Grams
   DevBuf basis[kMaxModes];   // per mode: last Ritz block (M x b, T)
   int basis_M[kMaxModes] = {0, 0, 0, 0};   // its M and b (0 = none)
   int basis_b[kMaxModes] = {0, 0, 0, 0};
@@ -201,6 +202,7 @@ void free_ws(Workspace& w, cudaStream_t s) {
   dev_free(w.A64, s);
   dev_free(w.gram64, s);
   dev_free(w.rinv, s);
+  dev_free(w.eig_part, s);
   w.ready = false;
 }
 
@@ -592,6 +594,7 @@ mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
   MACH_TRY(dev_alloc(w.rinv, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.fac[k], (size_t)h->dims[k] * ranks[k] * sizeof(T) + 64, st));
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.basis[k], (size_t)maxM * 32 * sizeof(T), st));
+  MACH_TRY(dev_alloc(w.eig_part, eig_part_elems((int)maxM) * sizeof(T), st));
   for (int k = 0; k < d; ++k) w.ranks[k] = ranks[k];
   w.ready = true;
   (void)maxI;
@@ -669,7 +672,7 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.U = w.U.ptr;
   e.Vout = static_cast<double*>(w.Vout.ptr);
   e.theta = static_cast<double*>(w.theta.ptr);
-  e.ctl = h->dscal()->eig_ctl;
+  e.part = w.eig_part.ptr;
   e.stats = h->dscal()->eig_stats;
   e.basis_out = w.basis[n].ptr;
   MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));

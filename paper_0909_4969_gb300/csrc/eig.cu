@@ -1,0 +1,708 @@
+// Leading eigenvectors of a small symmetric positive semi-definite Gram matrix
+// C (M x M): the "r_i leading left singular vectors" step of Algorithm 2 and
+// of HOSVD (Section 2.1), computed by block subspace iteration with a
+// Rayleigh-Ritz step in every iteration (the Lanczos-class "under-the-hood"
+// solver of Section 3 Remark 4).
+//
+// One iteration, with V (M x b) orthonormal:
+//   W = C V;  H = V^T W;  P = W^T W                       (M-length passes)
+//   H = Q Theta Q^T (cyclic Jacobi, one warp)             (b-space)
+//   E = W - V H,  F = E^T E;  residual of Ritz pair j:
+//       ||C u_j - theta_j u_j|| = sqrt(q_j^T F q_j)       (no cancellation)
+//   next basis V <- W Q D R^-1, R = chol(D Q^T P Q D), D = column scaling
+// All b x b work (Jacobi, Cholesky, the small products) runs on one warp in
+// shared memory; every M-length pass is a single sweep over rows.  Small
+// Grams (M <= 256) run in one CTA with operands in shared memory; larger
+// ones (HOSVD of long modes) run the same steps as multi-CTA launches with a
+// fixed iteration count.  A final Rayleigh-Ritz of the leading r Ritz vectors
+// is done in FP64.
+#include "mach_internal.cuh"
+
+namespace mach {
+
+namespace {
+
+constexpr int kEigThreads = 256;
+constexpr int kEigWarps = kEigThreads / 32;
+constexpr int kB = 32;        // maximum block width
+constexpr int kLd = kB + 1;   // padded leading dimension of b x b matrices
+constexpr int kEigSmallMax = 256;
+
+// ----------------------------------------------------------------------------
+// b-space helpers: one warp, matrices in shared memory with leading dim kLd.
+// ----------------------------------------------------------------------------
+
+// Cyclic Jacobi (Golub & Van Loan, sym.schur2 rotations; round-robin pair
+// ordering): H <- J^T H J until the off-diagonal mass is below rel_tol of the
+// diagonal, or stalls at the rounding floor.  Qm accumulates J (columns =
+// eigenvectors).  Lane i owns row i for the column updates and column i for
+// the row updates.
+template <typename T>
+__device__ void jacobi_warp(T* H, T* Qm, int n, T rel_tol, int max_sweeps, T* cs, int* pq) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j)
+    if (lane < n) Qm[lane * kLd + j] = (lane == j) ? T(1) : T(0);
+  __syncwarp();
+  if (n <= 1) return;
+  const int np = (n + 1) & ~1;
+  const int npairs = np / 2;
+  T prev_off = T(-1);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = T(0), dia = T(0);
+    if (lane < n)
+      for (int j = 0; j < n; ++j) {
+        const T h = H[lane * kLd + j];
+        if (j == lane) dia += h * h; else off += h * h;
+      }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if (off <= rel_tol * rel_tol * dia) break;
+    const T floor_rel = sizeof(T) == 8 ? T(1e-12) : T(1e-4);
+    if (prev_off >= T(0) && off > T(0.25) * prev_off && off <= floor_rel * floor_rel * dia) break;
+    prev_off = off;
+    for (int round = 0; round < np - 1; ++round) {
+      if (lane < npairs) {
+        const int pa = lane, pb = np - 1 - lane;
+        int p = pa == 0 ? 0 : ((pa - 1 + round) % (np - 1)) + 1;
+        int q = pb == 0 ? 0 : ((pb - 1 + round) % (np - 1)) + 1;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        T c = T(1), s = T(0);
+        if (q < n) {
+          const T hpq = H[p * kLd + q];
+          if (hpq != T(0)) {
+            const T tau = (H[q * kLd + q] - H[p * kLd + p]) / (T(2) * hpq);
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
+            s = t * c;
+          }
+        }
+        cs[2 * lane] = c;
+        cs[2 * lane + 1] = s;
+        pq[2 * lane] = p;
+        pq[2 * lane + 1] = q < n ? q : -1;
+      }
+      __syncwarp();
+      if (lane < n) {
+        for (int k = 0; k < npairs; ++k) {
+          const int q = pq[2 * k + 1];
+          if (q < 0) continue;
+          const int p = pq[2 * k];
+          const T c = cs[2 * k], s = cs[2 * k + 1];
+          const T hp = H[lane * kLd + p], hq = H[lane * kLd + q];
+          H[lane * kLd + p] = c * hp - s * hq;
+          H[lane * kLd + q] = s * hp + c * hq;
+          const T qp = Qm[lane * kLd + p], qq = Qm[lane * kLd + q];
+          Qm[lane * kLd + p] = c * qp - s * qq;
+          Qm[lane * kLd + q] = s * qp + c * qq;
+        }
+      }
+      __syncwarp();
+      if (lane < n) {
+        for (int k = 0; k < npairs; ++k) {
+          const int q = pq[2 * k + 1];
+          if (q < 0) continue;
+          const int p = pq[2 * k];
+          const T c = cs[2 * k], s = cs[2 * k + 1];
+          const T hp = H[p * kLd + lane], hq = H[q * kLd + lane];
+          H[p * kLd + lane] = c * hp - s * hq;
+          H[q * kLd + lane] = s * hp + c * hq;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// perm[0..n): indices of the diagonal of H in descending order (ties: lower index first).
+template <typename T>
+__device__ void sort_desc_warp(const T* H, int n, int* perm) {
+  const int lane = threadIdx.x & 31;
+  if (lane < n) {
+    const T v = H[lane * kLd + lane];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const T u = H[j * kLd + j];
+      rank += (u > v) || (u == v && j < lane);
+    }
+    perm[rank] = lane;
+  }
+  __syncwarp();
+}
+
+// In place upper Cholesky G = R^T R (right-looking, one warp); non-positive
+// pivots are replaced by a tiny positive value (columns that carry no
+// information then come out as noise that the next iteration discards).
+template <typename T>
+__device__ void chol_warp(T* G, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    T djj = G[j * kLd + j];
+    djj = djj > T(0) ? sqrt(djj) : T(1e-30);
+    __syncwarp();
+    if (lane == 0) G[j * kLd + j] = djj;
+    if (lane > j && lane < n) G[j * kLd + lane] /= djj;
+    __syncwarp();
+    if (lane > j && lane < n)
+      for (int c2 = lane; c2 < n; ++c2) G[lane * kLd + c2] -= G[j * kLd + lane] * G[j * kLd + c2];
+    __syncwarp();
+  }
+}
+
+// Shared state of one b-space step.
+template <typename T>
+struct BSpace {
+  T H[kB * kLd];    // V^T W, then diagonalised
+  T P[kB * kLd];    // W^T W
+  T F[kB * kLd];    // E^T E
+  T Q[kB * kLd];    // eigenvectors of H (unsorted columns)
+  T S[kB * kLd];    // next-basis transform (or sorted Q)
+  T G[kB * kLd];    // scratch
+  T cs[2 * kB];
+  int pq[2 * kB];
+  int perm[kB];
+  T theta[kB];
+  T d[kB];          // column scaling
+  int conv;
+};
+
+// Warp 0: Jacobi on H, sort, residual test (needs F unless `check` is false),
+// and, when not converged, S = Q_sorted D R^-1 with R = chol(D Q^T P Q D).
+// When converged (or `final_rotation`), S = Q_sorted (Ritz vectors U = V S).
+template <typename T>
+__device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev, bool check, bool final_rotation) {
+  const int lane = threadIdx.x & 31;
+  jacobi_warp<T>(s.H, s.Q, b, sizeof(T) == 8 ? T(1e-15) : T(1e-7), 20, s.cs, s.pq);
+  sort_desc_warp<T>(s.H, b, s.perm);
+  if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
+  // sorted eigenvectors into S
+  for (int j = 0; j < b; ++j)
+    if (lane < b) s.S[lane * kLd + j] = s.Q[lane * kLd + s.perm[j]];
+  __syncwarp();
+  bool conv = false;
+  if (check) {
+    // res_j^2 = q_j^T F q_j for the leading r Ritz pairs (lane j)
+    double res = 0.0;
+    if (lane < r) {
+      for (int a = 0; a < b; ++a) {
+        T fq = T(0);
+        for (int c = 0; c < b; ++c) fq += s.F[a * kLd + c] * s.S[c * kLd + lane];
+        res += (double)s.S[a * kLd + lane] * (double)fq;
+      }
+    }
+    res = res > 0.0 ? sqrt(res) : 0.0;
+    double worst = res;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    const double th0 = fabs((double)s.theta[0]);
+    const double rel = th0 > 0.0 ? worst / th0 : 0.0;
+    const bool floor_hit = rel < 10.0 * tol && rel > 0.5 * (*prev);
+    conv = (th0 == 0.0) || rel <= tol || floor_hit;
+    *prev = rel;
+  }
+  if (lane == 0) s.conv = conv ? 1 : 0;
+  if (conv || final_rotation) {
+    __syncwarp();
+    return;
+  }
+  // G = S^T P S (S = sorted Q), then column scaling D and Cholesky
+  for (int j = 0; j < b; ++j) {
+    if (lane < b) {
+      T acc = T(0);
+      for (int c = 0; c < b; ++c) acc += s.P[lane * kLd + c] * s.S[c * kLd + j];
+      s.G[lane * kLd + j] = acc;   // (P S)[lane][j]
+    }
+  }
+  __syncwarp();
+  T row[kB];
+  for (int j = 0; j < b; ++j) {
+    T acc = T(0);
+    if (lane < b)
+      for (int a = 0; a < b; ++a) acc += s.S[a * kLd + lane] * s.G[a * kLd + j];
+    row[j] = acc;   // (S^T P S)[lane][j]
+  }
+  __syncwarp();
+  for (int j = 0; j < b; ++j)
+    if (lane < b) s.G[lane * kLd + j] = row[j];
+  __syncwarp();
+  if (lane < b) {
+    const T g = s.G[lane * kLd + lane];
+    s.d[lane] = g > T(0) ? T(1) / sqrt(g) : T(0);
+  }
+  __syncwarp();
+  // D G D
+  if (lane < b)
+    for (int j = 0; j < b; ++j) s.G[lane * kLd + j] *= s.d[lane] * s.d[j];
+  __syncwarp();
+  chol_warp<T>(s.G, b);
+  // S <- S D R^-1 : row `lane` of S D, forward substitution against upper R
+  if (lane < b) {
+    for (int j = 0; j < b; ++j) row[j] = s.S[lane * kLd + j] * s.d[j];
+    for (int j = 0; j < b; ++j) {
+      T v = row[j];
+      for (int k = 0; k < j; ++k) v -= row[k] * s.G[k * kLd + j];
+      row[j] = v / s.G[j * kLd + j];
+    }
+    for (int j = 0; j < b; ++j) s.S[lane * kLd + j] = row[j];
+  }
+  __syncwarp();
+}
+
+// ----------------------------------------------------------------------------
+// M-length passes (all threads of a CTA, rows [i0, i1)).
+// ----------------------------------------------------------------------------
+
+// W[i, :ncols] = C[i, :] V[:, :ncols] for rows i in [i0, i1); warp per RPW
+// rows, lane j per column j of V (coalesced rows of V, broadcast C).
+template <typename T, int RPW>
+__device__ void cv_rows(const T* C, int M, const T* V, int b, T* W, int ncols, int i0, int i1, int warp, int nwarps) {
+  const int lane = threadIdx.x & 31;
+  for (int r0 = i0 + RPW * warp; r0 < i1; r0 += RPW * nwarps) {
+    const int nr = min(RPW, i1 - r0);
+    const T* crow[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) crow[q] = C + (size_t)(r0 + (q < nr ? q : 0)) * M;
+    T acc[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) acc[q] = T(0);
+    if (lane < ncols) {
+      const T* vc = V + lane;
+#pragma unroll 4
+      for (int k = 0; k < M; ++k) {
+        const T v = vc[(size_t)k * b];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) acc[q] += crow[q][k] * v;
+      }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q)
+        if (q < nr) W[(size_t)(r0 + q) * b + lane] = acc[q];
+    }
+  }
+}
+
+// Gram-type sums over rows [i0, i1): H += X^T Y, P += Y^T Y (when P != null).
+// Thread t owns entries t, t + 256, .. of the b x b results.
+template <typename T>
+__device__ void grams_rows(const T* X, const T* Y, int b, int i0, int i1, T* Hout, T* Pout, int ldo) {
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int p = e / b, q = e - (e / b) * b;
+    T h = T(0), g = T(0);
+    for (int i = i0; i < i1; ++i) {
+      const T yq = Y[(size_t)i * b + q];
+      h += X[(size_t)i * b + p] * yq;
+      if (Pout) g += Y[(size_t)i * b + p] * yq;
+    }
+    Hout[p * ldo + q] = h;
+    if (Pout) Pout[p * ldo + q] = g;
+  }
+}
+
+// E = W - V H for rows [i0, i1) (H from shared memory, ld kLd).
+template <typename T>
+__device__ void resid_rows(const T* V, const T* W, const T* H, int b, int i0, int i1, T* E) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    T vr[kB];
+#pragma unroll
+    for (int k = 0; k < kB; ++k) vr[k] = k < b ? V[(size_t)i * b + k] : T(0);
+    for (int j = 0; j < b; ++j) {
+      T acc = W[(size_t)i * b + j];
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (k < b) acc -= vr[k] * H[k * kLd + j];
+      E[(size_t)i * b + j] = acc;
+    }
+  }
+}
+
+// Out[i, :ncols] = X[i, :] S[:, :ncols] for rows [i0, i1) (S in shared memory, ld kLd).
+template <typename T>
+__device__ void apply_rows(const T* X, const T* S, int b, int ncols, T* Out, int ldout, int i0, int i1) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    T xr[kB];
+#pragma unroll
+    for (int k = 0; k < kB; ++k) xr[k] = k < b ? X[(size_t)i * b + k] : T(0);
+    for (int j = 0; j < ncols; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < kB; ++k)
+        if (k < b) acc += xr[k] * S[k * kLd + j];
+      Out[(size_t)i * ldout + j] = acc;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Final FP64 Rayleigh-Ritz of the leading r Ritz vectors U (M x b, first r
+// columns) with CU = C U (first r columns): H64 = U_r^T CU_r (FP64 sums),
+// FP64 Jacobi, Vout = U_r Q64, theta.  One CTA.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ void final_rr(const T* U, const T* CU, int M, int b, int r, double* Vout, double* theta, double* H64,
+                         double* Q64, double* cs64, int* pq, int* perm) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int p = e / r, q = e - (e / r) * r;
+    double s = 0.0;
+    for (int i = 0; i < M; ++i) s += (double)U[(size_t)i * b + p] * (double)CU[(size_t)i * b + q];
+    H64[p * kLd + q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // symmetrise
+    const int lane = threadIdx.x;
+    if (lane < r)
+      for (int j = lane + 1; j < r; ++j) {
+        const double avg = 0.5 * (H64[lane * kLd + j] + H64[j * kLd + lane]);
+        H64[lane * kLd + j] = avg;
+        H64[j * kLd + lane] = avg;
+      }
+    __syncwarp();
+    jacobi_warp<double>(H64, Q64, r, 1e-15, 30, cs64, pq);
+    sort_desc_warp<double>(H64, r, perm);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    double ur[kMaxRank];
+    for (int k = 0; k < r; ++k) ur[k] = (double)U[(size_t)i * b + k];
+    for (int j = 0; j < r; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < r; ++k) s += ur[k] * Q64[k * kLd + perm[j]];
+      Vout[(size_t)i * r + j] = s;
+    }
+  }
+  if (threadIdx.x < r) theta[threadIdx.x] = H64[perm[threadIdx.x] * kLd + perm[threadIdx.x]];
+  __syncthreads();
+}
+
+template <typename T>
+struct EigArgs {
+  const T* C;          // M x M symmetric (row-major)
+  int M, r, b;
+  T* V;                // M x b start block (global); overwritten (split path)
+  T* W;                // M x b scratch (global)
+  T* U;                // M x b scratch (global)
+  T* part;             // split path: partial b x b Grams, >= 3 * nblk * b * b
+  double* Vout;        // M x r FP64 eigenvectors (row-major)
+  double* theta;       // r FP64 eigenvalues, descending
+  int maxit;
+  double tol;
+  unsigned long long* stats;  // calls, iterations, unconverged
+  T* basis_out;        // M x b final Ritz block (warm start of the next solve), or null
+};
+
+// ----------------------------------------------------------------------------
+// Fused path: one CTA, M <= kEigSmallMax.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, int smem_mode) {
+  extern __shared__ __align__(16) unsigned char eig_smem[];
+  __shared__ BSpace<T> bs;
+  __shared__ double H64[kB * kLd], Q64[kB * kLd], cs64[2 * kB];
+  __shared__ double prev;
+  const int M = a.M, b = a.b, r = a.r;
+  const int warp = threadIdx.x >> 5;
+  T* V = a.V;
+  T* W = a.W;
+  T* U = a.U;
+  const T* C = a.C;
+  if (smem_mode >= 1) {
+    V = reinterpret_cast<T*>(eig_smem);
+    W = V + (size_t)M * b;
+    U = W + (size_t)M * b;
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = a.V[o];
+  }
+  if (smem_mode == 2) {
+    T* Cs = U + (size_t)M * b;
+    for (int o = threadIdx.x; o < M * M; o += blockDim.x) Cs[o] = a.C[o];
+    C = Cs;
+  }
+  if (threadIdx.x == 0) prev = 1e300;
+  __syncthreads();
+  // orthonormalise the start block: P = V^T V, S from its scaled Cholesky
+  grams_rows<T>(V, V, b, 0, M, bs.P, nullptr, kLd);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane < b) {
+      const T g = bs.P[lane * kLd + lane];
+      bs.d[lane] = g > T(0) ? T(1) / sqrt(g) : T(0);
+    }
+    __syncwarp();
+    if (lane < b)
+      for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
+    __syncwarp();
+    chol_warp<T>(bs.G, b);
+    // S = D R^-1 (upper): solve row by row of the identity scaled by D
+    if (lane < b) {
+      T row[kB];
+      for (int j = 0; j < b; ++j) row[j] = (j == lane) ? bs.d[lane] : T(0);
+      for (int j = 0; j < b; ++j) {
+        T v = row[j];
+        for (int k = 0; k < j; ++k) v -= row[k] * bs.G[k * kLd + j];
+        row[j] = v / bs.G[j * kLd + j];
+      }
+      for (int j = 0; j < b; ++j) bs.S[lane * kLd + j] = row[j];
+    }
+  }
+  __syncthreads();
+  apply_rows<T>(V, bs.S, b, b, W, b, 0, M);
+  __syncthreads();
+  for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = W[o];
+  __syncthreads();
+
+  int it = 0;
+  bool conv = false;
+  for (; it < a.maxit; ++it) {
+    cv_rows<T, 4>(C, M, V, b, W, b, 0, M, warp, kEigWarps);
+    __syncthreads();
+    grams_rows<T>(V, W, b, 0, M, bs.H, bs.P, kLd);
+    __syncthreads();
+    resid_rows<T>(V, W, bs.H, b, 0, M, U);   // U is free here
+    __syncthreads();
+    grams_rows<T>(U, U, b, 0, M, bs.F, nullptr, kLd);
+    __syncthreads();
+    if (threadIdx.x < 32) bspace_step<T>(bs, b, r, a.tol, &prev, true, it + 1 == a.maxit);
+    __syncthreads();
+    if (bs.conv || it + 1 == a.maxit) {
+      conv = bs.conv != 0;
+      apply_rows<T>(V, bs.S, b, b, U, b, 0, M);   // Ritz vectors
+      __syncthreads();
+      break;
+    }
+    apply_rows<T>(W, bs.S, b, b, U, b, 0, M);     // next basis (into U, then swap)
+    __syncthreads();
+    T* t = V;
+    V = U;
+    U = t;
+  }
+  if (a.maxit <= 0) {
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) U[o] = V[o];
+    __syncthreads();
+  }
+  if (a.basis_out)
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) a.basis_out[o] = U[o];
+  cv_rows<T, 4>(C, M, U, b, W, r, 0, M, warp, kEigWarps);
+  __syncthreads();
+  final_rr<T>(U, W, M, b, r, a.Vout, a.theta, H64, Q64, cs64, bs.pq, bs.perm);
+  if (threadIdx.x == 0 && a.stats) {
+    atomicAdd(&a.stats[0], 1ull);
+    atomicAdd(&a.stats[1], (unsigned long long)min(it + 1, max(a.maxit, 0)));
+    if (!conv) atomicAdd(&a.stats[2], 1ull);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Split path (large M): fixed iteration count, multi-CTA passes.
+// ----------------------------------------------------------------------------
+constexpr int kRowsPerCta = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) split_cv_kernel(const T* C, int M, const T* V, int b, T* W, int ncols) {
+  const int i0 = blockIdx.x * kRowsPerCta;
+  cv_rows<T, 4>(C, M, V, b, W, ncols, i0, min(M, i0 + kRowsPerCta), threadIdx.x >> 5, 8);
+}
+
+// partial Grams of a row block: part[blk][0] = V^T W, part[blk][1] = W^T W
+template <typename T>
+__global__ void __launch_bounds__(256) split_grams_kernel(const T* V, const T* W, int M, int b, T* part) {
+  const int i0 = blockIdx.x * kRowsPerCta;
+  T* h = part + (size_t)blockIdx.x * 2 * b * b;
+  grams_rows<T>(V, W, b, i0, min(M, i0 + kRowsPerCta), h, h + b * b, b);
+}
+
+// partial start Gram V^T V of a row block
+template <typename T>
+__global__ void __launch_bounds__(256) split_gram_vv_kernel(const T* V, int M, int b, T* part) {
+  const int i0 = blockIdx.x * kRowsPerCta;
+  grams_rows<T>(V, V, b, i0, min(M, i0 + kRowsPerCta), part + (size_t)blockIdx.x * 2 * b * b, nullptr, b);
+}
+
+// one CTA: reduce partials (fixed order), b-space step; S to global (b x b)
+template <typename T>
+__global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nblk, int b, int r, int mode,
+                                                           T* S_out) {
+  // mode 0: start block orthonormalisation (part holds V^T V)
+  // mode 1: iteration (next basis); mode 2: final (Ritz rotation)
+  __shared__ BSpace<T> bs;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    T h = T(0), g = T(0);
+    for (int k = 0; k < nblk; ++k) {
+      h += part[(size_t)k * 2 * b * b + e];
+      if (mode != 0) g += part[(size_t)k * 2 * b * b + b * b + e];
+    }
+    const int p = e / b, q = e - (e / b) * b;
+    if (mode == 0) bs.P[p * kLd + q] = h;
+    else {
+      bs.H[p * kLd + q] = h;
+      bs.P[p * kLd + q] = g;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (mode == 0) {
+      if (lane < b) {
+        const T g = bs.P[lane * kLd + lane];
+        bs.d[lane] = g > T(0) ? T(1) / sqrt(g) : T(0);
+      }
+      __syncwarp();
+      if (lane < b)
+        for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
+      __syncwarp();
+      chol_warp<T>(bs.G, b);
+      if (lane < b) {
+        T row[kB];
+        for (int j = 0; j < b; ++j) row[j] = (j == lane) ? bs.d[lane] : T(0);
+        for (int j = 0; j < b; ++j) {
+          T v = row[j];
+          for (int k = 0; k < j; ++k) v -= row[k] * bs.G[k * kLd + j];
+          row[j] = v / bs.G[j * kLd + j];
+        }
+        for (int j = 0; j < b; ++j) bs.S[lane * kLd + j] = row[j];
+      }
+    } else {
+      // symmetrise H (rounding) before Jacobi
+      if (lane < b)
+        for (int j = lane + 1; j < b; ++j) {
+          const T avg = T(0.5) * (bs.H[lane * kLd + j] + bs.H[j * kLd + lane]);
+          bs.H[lane * kLd + j] = avg;
+          bs.H[j * kLd + lane] = avg;
+        }
+      __syncwarp();
+      double prev = 1e300;
+      bspace_step<T>(bs, b, r, 0.0, &prev, false, mode == 2);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int p = e / b, q = e - (e / b) * b;
+    S_out[p * kB + q] = bs.S[p * kLd + q];
+  }
+}
+
+// Out = X S (rows of the CTA's block), S from global (b x b, ld kB)
+template <typename T>
+__global__ void __launch_bounds__(256) split_apply_kernel(const T* X, const T* S, int M, int b, T* Out) {
+  __shared__ T Ss[kB * kLd];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int p = e / b, q = e - (e / b) * b;
+    Ss[p * kLd + q] = S[p * kB + q];
+  }
+  __syncthreads();
+  const int i0 = blockIdx.x * kRowsPerCta;
+  apply_rows<T>(X, Ss, b, b, Out, b, i0, min(M, i0 + kRowsPerCta));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) split_final_kernel(EigArgs<T> a, const T* U, const T* CU, int iters) {
+  __shared__ double H64[kB * kLd], Q64[kB * kLd], cs64[2 * kB];
+  __shared__ int pq[2 * kB], perm[kB];
+  final_rr<T>(U, CU, a.M, a.b, a.r, a.Vout, a.theta, H64, Q64, cs64, pq, perm);
+  if (threadIdx.x == 0 && a.stats) {
+    atomicAdd(&a.stats[0], 1ull);
+    atomicAdd(&a.stats[1], (unsigned long long)iters);
+  }
+}
+
+template <typename T>
+__global__ void copy_kernel(const T* src, T* dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+}  // namespace
+
+int eig_split_threshold() { return kEigSmallMax; }
+
+size_t eig_part_elems(int M) { return (size_t)ceil_div(M, kRowsPerCta) * 2 * kB * kB + kB * kB; }
+
+template <typename T>
+mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
+  EigArgs<T> a;
+  a.C = C;
+  a.M = e.M;
+  a.r = e.r;
+  a.b = e.b;
+  a.V = static_cast<T*>(e.V);
+  a.W = static_cast<T*>(e.W);
+  a.U = static_cast<T*>(e.U);
+  a.part = static_cast<T*>(e.part);
+  a.Vout = e.Vout;
+  a.theta = e.theta;
+  a.maxit = e.maxit;
+  a.tol = e.tol;
+  a.stats = e.stats;
+  a.basis_out = static_cast<T*>(e.basis_out);
+  const int M = e.M, b = e.b;
+  if (M <= kEigSmallMax) {
+    cudaFuncAttributes fa;
+    MACH_CUDA_TRY(cudaFuncGetAttributes(&fa, eig_fused_kernel<T>));
+    int dev = 0, optin = 0;
+    MACH_CUDA_TRY(cudaGetDevice(&dev));
+    MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t budget = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
+    const size_t vwu = (size_t)3 * M * b * sizeof(T), cb = (size_t)M * M * sizeof(T);
+    int mode = 0;
+    size_t bytes = 0;
+    if (vwu + cb <= budget) {
+      mode = 2;
+      bytes = vwu + cb;
+    } else if (vwu <= budget) {
+      mode = 1;
+      bytes = vwu;
+    }
+    MACH_CUDA_TRY(cudaFuncSetAttribute(eig_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    eig_fused_kernel<T><<<1, kEigThreads, bytes, st>>>(a, mode);
+    MACH_LAUNCH_CHECK();
+    return MACH_OK;
+  }
+  // split path: V0 -> orthonormal V; fixed iterations; final rotation and FP64 Rayleigh-Ritz
+  const int nblk = (int)ceil_div(M, kRowsPerCta);
+  T* part = a.part;
+  T* S = part + (size_t)nblk * 2 * b * b;
+  T* V = a.V;
+  T* W = a.W;
+  T* U = a.U;
+  split_gram_vv_kernel<T><<<nblk, 256, 0, st>>>(V, M, b, part);
+  MACH_LAUNCH_CHECK();
+  split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, 0, S);
+  MACH_LAUNCH_CHECK();
+  split_apply_kernel<T><<<nblk, 256, 0, st>>>(V, S, M, b, W);
+  MACH_LAUNCH_CHECK();
+  std::swap(V, W);
+  const int iters = std::max(1, e.maxit);
+  for (int it = 0; it < iters; ++it) {
+    split_cv_kernel<T><<<nblk, 256, 0, st>>>(C, M, V, b, W, b);
+    MACH_LAUNCH_CHECK();
+    split_grams_kernel<T><<<nblk, 256, 0, st>>>(V, W, M, b, part);
+    MACH_LAUNCH_CHECK();
+    const bool last = it + 1 == iters;
+    split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, last ? 2 : 1, S);
+    MACH_LAUNCH_CHECK();
+    if (last) {
+      split_apply_kernel<T><<<nblk, 256, 0, st>>>(V, S, M, b, U);   // Ritz vectors
+      MACH_LAUNCH_CHECK();
+    } else {
+      split_apply_kernel<T><<<nblk, 256, 0, st>>>(W, S, M, b, U);   // next basis
+      MACH_LAUNCH_CHECK();
+      std::swap(V, U);
+    }
+  }
+  if (a.basis_out) {
+    copy_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024), 256, 0, st>>>(
+        U, a.basis_out, (int64_t)M * b);
+    MACH_LAUNCH_CHECK();
+  }
+  split_cv_kernel<T><<<nblk, 256, 0, st>>>(C, M, U, b, W, e.r);
+  MACH_LAUNCH_CHECK();
+  split_final_kernel<T><<<1, 256, 0, st>>>(a, U, W, iters);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+template mach_status launch_eig<float>(const float*, const EigLaunch&, cudaStream_t);
+template mach_status launch_eig<double>(const double*, const EigLaunch&, cudaStream_t);
+
+}  // namespace mach

@@ -318,10 +318,12 @@ struct EigLaunch {
   void* U;
   double* Vout;
   double* theta;
-  void* ctl;                   // >= 64 bytes of device scratch (split path)
+  void* part;                  // >= eig_part_elems(M) elements of T (split path)
   unsigned long long* stats;   // device counters: calls, iterations, unconverged
   void* basis_out;             // M x b T: final Ritz block, or null
 };
+int eig_split_threshold();
+size_t eig_part_elems(int M);
 template <typename T>
 mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st);
 template <typename T>
