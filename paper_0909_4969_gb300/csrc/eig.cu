@@ -133,23 +133,52 @@ __device__ void sort_desc_warp(const T* H, int n, int* perm) {
   __syncwarp();
 }
 
-// In place upper Cholesky G = R^T R (right-looking, one warp); non-positive
-// pivots are replaced by a tiny positive value (columns that carry no
-// information then come out as noise that the next iteration discards).
+// In place upper Cholesky G = R^T R (right-looking, one warp) of a Gram with
+// unit (or zero) diagonal, rank-revealing: a column whose pivot falls below
+// the arithmetic's floor depends numerically on the earlier ones; it is
+// marked dead (dead[j] = 1, R row j = e_j^T) and the caller zeroes it.
 template <typename T>
-__device__ void chol_warp(T* G, int n) {
+__device__ void chol_warp(T* G, int n, int* dead) {
   const int lane = threadIdx.x & 31;
+  const T floor_piv = sizeof(T) == 8 ? T(1e-24) : T(1e-10);
   for (int j = 0; j < n; ++j) {
-    T djj = G[j * kLd + j];
-    djj = djj > T(0) ? sqrt(djj) : T(1e-30);
+    const T piv = G[j * kLd + j];
+    const bool is_dead = !(piv > floor_piv);
     __syncwarp();
-    if (lane == 0) G[j * kLd + j] = djj;
+    if (is_dead) {
+      if (lane == 0) {
+        G[j * kLd + j] = T(1);
+        dead[j] = 1;
+      }
+      if (lane > j && lane < n) G[j * kLd + lane] = T(0);
+      __syncwarp();
+      continue;
+    }
+    const T djj = sqrt(piv);
+    if (lane == 0) {
+      G[j * kLd + j] = djj;
+      dead[j] = 0;
+    }
     if (lane > j && lane < n) G[j * kLd + lane] /= djj;
     __syncwarp();
     if (lane > j && lane < n)
       for (int c2 = lane; c2 < n; ++c2) G[lane * kLd + c2] -= G[j * kLd + lane] * G[j * kLd + c2];
     __syncwarp();
   }
+}
+
+// Column scaling of a Gram: d_j = 1/sqrt(G_jj), or 0 for columns whose norm
+// is negligible against the largest one.
+template <typename T>
+__device__ void col_scale_warp(const T* G, int n, T* d) {
+  const int lane = threadIdx.x & 31;
+  T g = lane < n ? G[lane * kLd + lane] : T(0);
+  T gmax = g;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  const T rel = sizeof(T) == 8 ? T(1e-28) : T(1e-12);
+  if (lane < n) d[lane] = (g > rel * gmax && g > T(0)) ? T(1) / sqrt(g) : T(0);
+  __syncwarp();
 }
 
 // Shared state of one b-space step.
@@ -166,6 +195,7 @@ struct BSpace {
   int perm[kB];
   T theta[kB];
   T d[kB];          // column scaling
+  int dead[kB];     // columns dropped by the rank-revealing Cholesky
   int conv;
 };
 
@@ -228,23 +258,19 @@ __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev
   for (int j = 0; j < b; ++j)
     if (lane < b) s.G[lane * kLd + j] = row[j];
   __syncwarp();
-  if (lane < b) {
-    const T g = s.G[lane * kLd + lane];
-    s.d[lane] = g > T(0) ? T(1) / sqrt(g) : T(0);
-  }
-  __syncwarp();
+  col_scale_warp<T>(s.G, b, s.d);
   // D G D
   if (lane < b)
     for (int j = 0; j < b; ++j) s.G[lane * kLd + j] *= s.d[lane] * s.d[j];
   __syncwarp();
-  chol_warp<T>(s.G, b);
+  chol_warp<T>(s.G, b, s.dead);
   // S <- S D R^-1 : row `lane` of S D, forward substitution against upper R
   if (lane < b) {
     for (int j = 0; j < b; ++j) row[j] = s.S[lane * kLd + j] * s.d[j];
     for (int j = 0; j < b; ++j) {
       T v = row[j];
       for (int k = 0; k < j; ++k) v -= row[k] * s.G[k * kLd + j];
-      row[j] = v / s.G[j * kLd + j];
+      row[j] = s.dead[j] ? T(0) : v / s.G[j * kLd + j];
     }
     for (int j = 0; j < b; ++j) s.S[lane * kLd + j] = row[j];
   }
@@ -425,15 +451,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    if (lane < b) {
-      const T g = bs.P[lane * kLd + lane];
-      bs.d[lane] = g > T(0) ? T(1) / sqrt(g) : T(0);
-    }
-    __syncwarp();
+    col_scale_warp<T>(bs.P, b, bs.d);
     if (lane < b)
       for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
     __syncwarp();
-    chol_warp<T>(bs.G, b);
+    chol_warp<T>(bs.G, b, bs.dead);
     // S = D R^-1 (upper): solve row by row of the identity scaled by D
     if (lane < b) {
       T row[kB];
@@ -441,7 +463,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
       for (int j = 0; j < b; ++j) {
         T v = row[j];
         for (int k = 0; k < j; ++k) v -= row[k] * bs.G[k * kLd + j];
-        row[j] = v / bs.G[j * kLd + j];
+        row[j] = bs.dead[j] ? T(0) : v / bs.G[j * kLd + j];
       }
       for (int j = 0; j < b; ++j) bs.S[lane * kLd + j] = row[j];
     }
@@ -543,22 +565,18 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     if (mode == 0) {
-      if (lane < b) {
-        const T g = bs.P[lane * kLd + lane];
-        bs.d[lane] = g > T(0) ? T(1) / sqrt(g) : T(0);
-      }
-      __syncwarp();
+      col_scale_warp<T>(bs.P, b, bs.d);
       if (lane < b)
         for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
       __syncwarp();
-      chol_warp<T>(bs.G, b);
+      chol_warp<T>(bs.G, b, bs.dead);
       if (lane < b) {
         T row[kB];
         for (int j = 0; j < b; ++j) row[j] = (j == lane) ? bs.d[lane] : T(0);
         for (int j = 0; j < b; ++j) {
           T v = row[j];
           for (int k = 0; k < j; ++k) v -= row[k] * bs.G[k * kLd + j];
-          row[j] = v / bs.G[j * kLd + j];
+          row[j] = bs.dead[j] ? T(0) : v / bs.G[j * kLd + j];
         }
         for (int j = 0; j < b; ++j) bs.S[lane * kLd + j] = row[j];
       }
