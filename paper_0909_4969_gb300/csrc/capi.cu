@@ -143,6 +143,7 @@ struct Workspace {
   DevBuf fac[kMaxModes];  // T row-major I_k x r_k
   DevBuf Y, partial, C, gram_part, V, W, U, Vout, theta, A64, gram64, rinv;
   DevBuf eig_part;           // split-path partial Grams
+  DevBuf ytpart;             // partials of the warm-start product Y^T A
   DevBuf basis[kMaxModes];   // per mode: last Ritz block (M x b, T)
   int basis_M[kMaxModes] = {0, 0, 0, 0};   // its M and b (0 = none)
   int basis_b[kMaxModes] = {0, 0, 0, 0};
@@ -203,6 +204,7 @@ void free_ws(Workspace& w, cudaStream_t s) {
   dev_free(w.gram64, s);
   dev_free(w.rinv, s);
   dev_free(w.eig_part, s);
+  dev_free(w.ytpart, s);
   w.ready = false;
 }
 
@@ -590,7 +592,9 @@ mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
   MACH_TRY(dev_alloc(w.Vout, (size_t)maxM * kMaxRank * sizeof(double), st));
   MACH_TRY(dev_alloc(w.theta, (size_t)32 * sizeof(double), st));
   MACH_TRY(dev_alloc(w.A64, (size_t)maxIr * sizeof(double), st));
-  MACH_TRY(dev_alloc(w.gram64, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
+  // per-CTA partial Grams of the FP64 Cholesky QR (lsv_finish grid <= 2 SMs worth)
+  MACH_TRY(dev_alloc(w.gram64, (size_t)(2 * num_sms() + 2) * kMaxRank * kMaxRank * sizeof(double), st));
+  MACH_TRY(dev_alloc(w.ytpart, (size_t)64 * std::max<int64_t>(maxM, 1) * kMaxRank * sizeof(T), st));
   MACH_TRY(dev_alloc(w.rinv, (size_t)kMaxRank * kMaxRank * sizeof(double), st));
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.fac[k], (size_t)h->dims[k] * ranks[k] * sizeof(T) + 64, st));
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.basis[k], (size_t)maxM * 32 * sizeof(T), st));
@@ -650,7 +654,7 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   const int M = jroute ? J : I;
   const int b = block_size_for(M, r, !warm);
   MACH_TRY(launch_start_block<T>(static_cast<const T*>(w.Y.ptr), static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
-                                 jroute, warm, static_cast<T*>(w.V.ptr), static_cast<T*>(w.U.ptr),
+                                 jroute, warm, static_cast<T*>(w.V.ptr), static_cast<T*>(w.ytpart.ptr),
                                  0x1000u + (uint32_t)n, st));
   // Columns r..b of the start block: the previous solve's Ritz vectors of the
   // same Gram shape, when there is one (the next directions after the top r).

@@ -174,52 +174,83 @@ __global__ void copy_cols(const T* __restrict__ A, int M, int r, T* V, int b) {
 // Factor from eigenvectors:
 //  J-route: A64[i][k] = sum_j Y[i][j] Vout[j][k] / sqrt(theta_k)   (FP64)
 //  I-route: A64 = Vout.
-// Then FP64 Cholesky QR: G = A^T A (atomics into gram64), last block
-// factors G = R^T R and stores R^-1 (upper) in rinv.
+// Then FP64 Cholesky QR: every CTA writes its partial Gram A_blk^T A_blk to
+// part[blockIdx] (register accumulation per lane, warp partials reduced in
+// shared memory); the last CTA to finish sums the partials in block order
+// (deterministic), factors G = R^T R and stores R^-1 (upper) in rinv.
 // ----------------------------------------------------------------------------
+constexpr int kPairsPerLane = (kMaxRank * kMaxRank + 31) / 32;
+
 template <typename T>
-__global__ void lsv_apply_kernel(const T* __restrict__ Y, const double* __restrict__ Vout,
-                                 const double* __restrict__ theta, int I, int J, int r, int jroute,
-                                 double* __restrict__ A64, double* gram64, unsigned* counter, double* rinv,
-                                 unsigned* err) {
-  __shared__ double sG[kMaxRank * kMaxRank];
+__global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y, const double* __restrict__ Vout,
+                                                        const double* __restrict__ theta, int I, int J, int r,
+                                                        int jroute, double* __restrict__ A64, double* part,
+                                                        unsigned* counter, double* rinv, unsigned* err) {
+  __shared__ double wsum[8][kMaxRank * kMaxRank];
   __shared__ double sinv[kMaxRank];
   __shared__ bool last;
-  for (int k = threadIdx.x; k < r * r; k += blockDim.x) sG[k] = 0.0;
   if (threadIdx.x < r) sinv[threadIdx.x] = theta[threadIdx.x] > 0.0 ? 1.0 / sqrt(theta[threadIdx.x]) : 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rr = r * r;
+  double gacc[kPairsPerLane];
+#pragma unroll
+  for (int k = 0; k < kPairsPerLane; ++k) gacc[k] = 0.0;
   for (int i = blockIdx.x * nw + warp; i < I; i += gridDim.x * nw) {
     double arow[kMaxRank];
     if (jroute) {
-      double s[kMaxRank];
-      for (int k = 0; k < kMaxRank; ++k) s[k] = 0.0;
+      double sacc[kMaxRank];
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k) sacc[k] = 0.0;
       for (int j = lane; j < J; j += 32) {
         const double y = (double)Y[(size_t)i * J + j];
-        for (int k = 0; k < r; ++k) s[k] += y * Vout[(size_t)j * r + k];
+#pragma unroll
+        for (int k = 0; k < kMaxRank; ++k)
+          if (k < r) sacc[k] += y * Vout[(size_t)j * r + k];
       }
-      for (int k = 0; k < r; ++k) arow[k] = warp_sum(s[k]) * sinv[k];
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? warp_sum(sacc[k]) * sinv[k] : 0.0;
     } else {
-      for (int k = 0; k < r; ++k) arow[k] = Vout[(size_t)i * r + k];
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? Vout[(size_t)i * r + k] : 0.0;
     }
-    if (lane < r) A64[(size_t)i * r + lane] = arow[lane];
-    // partial Gram
-    for (int pidx = lane; pidx < r * r; pidx += 32) {
-      const int p = pidx / r, q = pidx - (pidx / r) * r;
-      atomicAdd(&sG[pidx], arow[p] * arow[q]);
+    if (lane < r) A64[(size_t)i * r + lane] = arow[lane < kMaxRank ? lane : 0];
+#pragma unroll
+    for (int k = 0; k < kPairsPerLane; ++k) {
+      const int pidx = lane + 32 * k;
+      if (pidx < rr) {
+        const int p = pidx / r, q = pidx - (pidx / r) * r;
+        gacc[k] += arow[p] * arow[q];
+      }
     }
   }
+#pragma unroll
+  for (int k = 0; k < kPairsPerLane; ++k) {
+    const int pidx = lane + 32 * k;
+    if (pidx < rr) wsum[warp][pidx] = gacc[k];
+  }
   __syncthreads();
-  for (int k = threadIdx.x; k < r * r; k += blockDim.x) atomicAdd(&gram64[k], sG[k]);
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += wsum[w][e];
+    part[(size_t)blockIdx.x * rr + e] = t;
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  // Cholesky of gram64 (volatile reads of the accumulated values)
+  // deterministic sum of the partials (block order), then Cholesky (thread 0)
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+    double t = 0.0;
+    for (unsigned k = 0; k < gridDim.x; ++k) t += ((volatile double*)part)[(size_t)k * rr + e];
+    wsum[0][e] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double R[kMaxRank * kMaxRank];
-  for (int k = 0; k < r * r; ++k) R[k] = ((volatile double*)gram64)[k];
+  for (int k = 0; k < rr; ++k) R[k] = wsum[0][k];
   for (int j = 0; j < r; ++j) {
     double djj = R[j * r + j];
     for (int k = 0; k < j; ++k) djj -= R[k * r + j] * R[k * r + j];
@@ -238,7 +269,7 @@ __global__ void lsv_apply_kernel(const T* __restrict__ Y, const double* __restri
   }
   // inverse of upper-triangular R
   double Ri[kMaxRank * kMaxRank];
-  for (int k = 0; k < r * r; ++k) Ri[k] = 0.0;
+  for (int k = 0; k < rr; ++k) Ri[k] = 0.0;
   for (int j = 0; j < r; ++j) {
     Ri[j * r + j] = 1.0 / R[j * r + j];
     for (int i = j - 1; i >= 0; --i) {
@@ -247,7 +278,7 @@ __global__ void lsv_apply_kernel(const T* __restrict__ Y, const double* __restri
       Ri[i * r + j] = -v / R[i * r + i];
     }
   }
-  for (int k = 0; k < r * r; ++k) rinv[k] = Ri[k];
+  for (int k = 0; k < rr; ++k) rinv[k] = Ri[k];
 }
 
 // A = A64 R^-1: FP64 column-major output (I x r) and the row-major copy in T.
@@ -296,9 +327,9 @@ template <typename T>
 mach_status launch_gram(const T* Z, int64_t L, int M, int64_t sl, int64_t sm, T* C, T* partial_scratch,
                         int64_t partial_cap, cudaStream_t st) {
   const int tiles = (M + 31) / 32;
-  int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, L / 256), 64);
   const int ntiles = tiles * (tiles + 1) / 2;
-  while (nsplit > 1 && (int64_t)ntiles * nsplit > 4 * num_sms()) nsplit /= 2;
+  int nsplit = (int)std::min<int64_t>(std::max<int64_t>(1, L / 32), std::max(1, num_sms() / ntiles));
+  nsplit = std::min(nsplit, 64);
   if ((int64_t)nsplit * M * M > partial_cap) nsplit = 1;
   dim3 grid(tiles, tiles, nsplit);
   if (nsplit == 1) {
@@ -338,9 +369,9 @@ mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, 
   MACH_LAUNCH_CHECK();
   if (warm) {
     if (jroute) {
-      // partials (nsplit x J x r) live in `scratch`, which holds J x 32
-      // elements, so nsplit <= 32 / r
-      const int nsplit = std::max(1, std::min(32 / std::max(r, 1), std::max(1, I / 64)));
+      // partials (nsplit x J x r) live in `scratch` (>= 64 J kMaxRank elements)
+      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(
+          std::min<int64_t>(64, std::max<int64_t>(1, I / 16)), num_sms() / std::max<int64_t>(1, ceil_div(J, 32))));
       T* part = scratch;
       yt_times_a_part<T><<<dim3((unsigned)ceil_div(J, 32), (unsigned)nsplit), 256, 0, st>>>(Y, Aprev, I, J, r, nsplit,
                                                                                            part);
@@ -358,7 +389,6 @@ template <typename T>
 mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* theta, int I, int J, int r, bool jroute,
                               double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
                               double* out_colmajor, T* out_rowmajor, cudaStream_t st) {
-  MACH_CUDA_TRY(cudaMemsetAsync(gram64, 0, sizeof(double) * r * r, st));
   MACH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 8), 2 * num_sms()));
   lsv_apply_kernel<T><<<blocks, 256, 0, st>>>(Y, Vout, theta, I, J, r, jroute ? 1 : 0, A64, gram64, counter, rinv,

@@ -164,6 +164,13 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
     T acc[ACC];
 #pragma unroll
     for (int s = 0; s < ACC; ++s) acc[s] = T(0);
+    // d = 3: lane (h, am) = (lane >> 4, lane & 15) folds the fibres j = h,
+    // h + 2, .. into row am of the (r_mid x r_leaf) block: acc3[b] +=
+    // A_mid[i_mid(f_j), am] z_j[b]  (z_j read as a broadcast)
+    T acc3[D == 3 ? RLM : 1];
+#pragma unroll
+    for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] = T(0);
+    const int half = lane >> 4, am = lane & 15;
     T w[D == 4 ? kSQ : 1];
 #pragma unroll
     for (int s = 0; s < (D == 4 ? kSQ : 1); ++s) w[s] = T(0);
@@ -226,6 +233,18 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
       smid[warp][lane] = mid;
       __syncwarp();
       const int nv = __popc(vm);
+      if (D == 3) {
+        if (am < a.r_mid0) {
+          for (int j = half; j < nv; j += 2) {
+            const T m = Amid0[(size_t)smid[warp][j] * a.r_mid0 + am];
+            const T* zj = sz[warp][j];
+#pragma unroll
+            for (int b = 0; b < RLM; ++b) acc3[b] += m * zj[b];
+          }
+        }
+        __syncwarp();
+        continue;
+      }
       for (int j = 0; j < nv; ++j) {
         const T* zj = sz[warp][j];
         if (D == 2) {
@@ -264,6 +283,14 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
             if (s < SQ && q < Q && r1 * SQ + s < ACC) dst[r1 * Q + q] = acc[r1 * SQ + s];
           }
         }
+      }
+    } else if (D == 3) {
+#pragma unroll
+      for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] += __shfl_xor_sync(0xffffffffu, acc3[b], 16);
+      if (half == 0 && am < a.r_mid0) {
+#pragma unroll
+        for (int b = 0; b < (D == 3 ? RLM : 1); ++b)
+          if (b < rl) dst[am * rl + b] = acc3[b];
       }
     } else {
 #pragma unroll
@@ -365,13 +392,7 @@ static mach_status launch_ttmc_rl(const TtmcLaunch& L, cudaStream_t st) {
 template <typename V, typename T>
 static mach_status launch_ttmc_vt(const TtmcLaunch& L, cudaStream_t st) {
   if (L.d == 2) return launch_ttmc_rl<V, T, 2, 1>(L, st);
-  if (L.d == 3) {
-    const int need = (L.J + 31) / 32;
-    if (need <= 1) return launch_ttmc_rl<V, T, 3, 1>(L, st);
-    if (need <= 2) return launch_ttmc_rl<V, T, 3, 2>(L, st);
-    if (need <= 4) return launch_ttmc_rl<V, T, 3, 4>(L, st);
-    return launch_ttmc_rl<V, T, 3, 8>(L, st);
-  }
+  if (L.d == 3) return launch_ttmc_rl<V, T, 3, 1>(L, st);   // half-warp fold: no ACC slots
   if (L.d == 4) {
     const int Q = L.r_mid1 * L.r_leaf;
     const int need = L.r_mid0 * ((Q + 31) / 32);
