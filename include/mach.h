@@ -104,6 +104,45 @@ const char* mach_version(void);
 mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims,
                         double p, uint64_t seed, void* stream, mach_sample_t* out);
 
+/* ---------------------------------------------------------------------------
+ * mach_sample_noalloc — the same coin and compaction as mach_sample (Section
+ * 3 Remark 1; Algorithm 1 and 2, first block), written straight into
+ * caller-owned buffers, with NO allocation of any kind: no device or host
+ * heap memory, no memory pool, no library routine that allocates.  The paper
+ * has no counterpart; it exists for callers that must not allocate while
+ * they sample: a process whose device memory is entirely committed to
+ * resident tensors and preallocated output slabs (an allocation would fail
+ * or evict), and a caller on a latency-critical path where an allocator
+ * call could synchronise the device or stall behind other users of the
+ * pool.  The look-back scratch lives in a fixed 4 MiB device array inside
+ * libmach (one copy per device), which limits one call to
+ * 2,147,471,360 FP32 or 1,073,735,680 FP64 entries.
+ *
+ *   x_dev, dtype, d, dims, p, seed  as for mach_sample.
+ *   idx_dev  device int64[cap]: receives the kept linear indices, increasing.
+ *   val_dev  device buffer of cap elements of `dtype`: the kept values,
+ *            unscaled, in the same order.  Both caller-owned, written only
+ *            in [0, min(cap, n_kept)).
+ *   cap      capacity of idx_dev / val_dev in entries (may be 0).
+ *   n_kept   host pointer receiving the number of kept entries, also when
+ *            it exceeds cap.
+ *   stream   work is ordered on it; the call synchronises it once, at the
+ *            end, to read the count.
+ * The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress), which may load the library's device code; make it
+ * once on every device before any stream capture or other context in which
+ * that lookup is not allowed.  Calls that overlap in time on one device
+ * (several host threads or streams) race on the single scratch array and
+ * give wrong results: serialise them.
+ * Errors: MACH_EINVAL (as for mach_sample; misaligned idx_dev / val_dev;
+ * N above the fixed-scratch limit, checked before any device work; cap <
+ * n_kept, after the work, with n_kept set and the first cap entries
+ * written), MACH_ECUDA, MACH_ETIMEOUT.
+ */
+mach_status mach_sample_noalloc(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims,
+                                double p, uint64_t seed, int64_t* idx_dev, void* val_dev,
+                                int64_t cap, int64_t* n_kept, void* stream);
+
 /* Number of kept entries (host value; no device work). */
 mach_status mach_sample_count(mach_sample_t s, int64_t* n_kept);
 

@@ -799,6 +799,55 @@ mach_status mach_core(mach_sample_t s, const int* ranks, double* const* factors_
                              1.0 / s->p, core_dev, st);
 }
 
+mach_status mach_sample_noalloc(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p,
+                                uint64_t seed, int64_t* idx_dev, void* val_dev, int64_t cap, int64_t* n_kept,
+                                void* stream) {
+  if (!x_dev || !dims || !n_kept || cap < 0) return MACH_EINVAL;
+  if (cap > 0 && (!idx_dev || !val_dev)) return MACH_EINVAL;
+  if (d < 2 || d > kMaxModes) return MACH_EINVAL;
+  if (dtype != MACH_F32 && dtype != MACH_F64) return MACH_EINVAL;
+  if (!(p > 0.0 && p <= 1.0)) return MACH_EINVAL;
+  const size_t vs = dtype_size(dtype);
+  if (((uintptr_t)x_dev & 15u) != 0 || ((uintptr_t)idx_dev & 7u) != 0 || ((uintptr_t)val_dev & (vs - 1)) != 0) {
+    set_last_error("x_dev must be 16-byte aligned, idx_dev and val_dev aligned to their element size");
+    return MACH_EINVAL;
+  }
+  int64_t N = 1;
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1 || dims[k] > kMaxDim) {
+      set_last_error("dims[%d] = %lld outside [1, %d]", k, (long long)dims[k], kMaxDim);
+      return MACH_EINVAL;
+    }
+    N *= dims[k];
+  }
+  const int64_t max_n = sampler_fixed_max_entries(dtype);
+  if (N > max_n) {
+    set_last_error("mach_sample_noalloc: %lld entries exceed the fixed scratch limit of %lld entries for this dtype",
+                   (long long)N, (long long)max_n);
+    return MACH_EINVAL;
+  }
+  unsigned long long* fixed = nullptr;
+  MACH_TRY(sampler_fixed_scratch(&fixed));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t T = (uint64_t)std::floor(p * 4294967296.0);
+  int64_t* d_count = reinterpret_cast<int64_t*>(fixed);
+  unsigned* d_err = reinterpret_cast<unsigned*>(fixed + 1);
+  // the status word starts at zero; the count and the look-back words are
+  // cleared by the launcher
+  MACH_CUDA_TRY(cudaMemsetAsync(fixed + 1, 0, sizeof(unsigned long long), st));
+  MACH_TRY(launch_sampler(x_dev, dtype, N, seed, T, cap, idx_dev, val_dev, d_count, d_err, fixed + 2, st));
+  unsigned long long h[2] = {0, 0};
+  MACH_CUDA_TRY(cudaMemcpyAsync(h, fixed, sizeof(h), cudaMemcpyDeviceToHost, st));
+  MACH_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h[1] & DEV_TIMEOUT) return MACH_ETIMEOUT;
+  *n_kept = (int64_t)h[0];
+  if ((int64_t)h[0] > cap) {
+    set_last_error("mach_sample_noalloc: %lld entries kept, capacity %lld", (long long)h[0], (long long)cap);
+    return MACH_EINVAL;
+  }
+  return MACH_OK;
+}
+
 mach_status mach_error(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, const int* ranks,
                        double* const* factors_dev, const double* core_dev, double* rel_err, double* x_norm,
                        void* stream) {

@@ -251,6 +251,11 @@ int num_sms();
 // linalg.cu / error.cu) and their argument blocks.
 // ----------------------------------------------------------------------------
 int64_t sampler_scratch_words(int64_t n, mach_dtype dt);
+// Fixed scratch of the allocation-free sampler (sample.cu): its size in
+// 8-byte words, the largest tensor it serves, and this device's address of it.
+constexpr int64_t kFixedScratchWords = 524288;
+int64_t sampler_fixed_max_entries(mach_dtype dt);
+mach_status sampler_fixed_scratch(unsigned long long** out);
 mach_status launch_sampler(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, int64_t cap,
                            int64_t* idx, void* val, int64_t* d_count, unsigned* d_err,
                            unsigned long long* scratch, cudaStream_t st);

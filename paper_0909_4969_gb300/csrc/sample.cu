@@ -17,6 +17,8 @@
 // Philox is evaluated exactly once per counter; every wait is bounded.
 #include "mach_internal.cuh"
 
+#include <mutex>
+
 namespace mach {
 
 namespace {
@@ -354,6 +356,41 @@ mach_status launch_sampler(const void* x, mach_dtype dt, int64_t n, uint64_t see
   if (dt == MACH_F32)
     return launch_sampler_t<float>(x, n, seed, T, cap, idx, val, d_count, d_err, scratch, st);
   return launch_sampler_t<double>(x, n, seed, T, cap, idx, val, d_count, d_err, scratch, st);
+}
+
+}  // namespace mach
+
+// ----------------------------------------------------------------------------
+// Fixed device scratch of the allocation-free sampling entry point: word 0
+// the kept count, word 1 the status bits, word 2 the tile counter, words
+// 3.. the look-back status of each tile.  4 MiB: 524285 tiles, i.e. up to
+// 2,147,471,360 FP32 or 1,073,735,680 FP64 entries per call.  One copy per
+// device, so calls that overlap on one device race on it.
+// ----------------------------------------------------------------------------
+static __device__ __align__(256) unsigned long long g_sampler_fixed_scratch[mach::kFixedScratchWords];
+
+namespace mach {
+
+int64_t sampler_fixed_max_entries(mach_dtype dt) {
+  const int64_t tile = dt == MACH_F32 ? SampCfg<float>::kTile : SampCfg<double>::kTile;
+  return (kFixedScratchWords - 3) * tile;
+}
+
+mach_status sampler_fixed_scratch(unsigned long long** out) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static unsigned long long* addr[kMaxDevices] = {};
+  int dev = 0;
+  MACH_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return MACH_EINVAL;
+  std::lock_guard<std::mutex> g(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    MACH_CUDA_TRY(cudaGetSymbolAddress(&p, g_sampler_fixed_scratch));
+    addr[dev] = static_cast<unsigned long long*>(p);
+  }
+  *out = addr[dev];
+  return MACH_OK;
 }
 
 }  // namespace mach

@@ -32,6 +32,9 @@ SIGNATURES = {
     "mach_version": (ctypes.c_char_p, []),
     "mach_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mach_sample_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
+                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           _c_i64p, ctypes.c_void_p]),
     "mach_sample_count": (ctypes.c_int, [ctypes.c_void_p, _c_i64p]),
     "mach_sample_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "mach_sample_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -213,6 +216,29 @@ class Sample:
 
 def sample(x: torch.Tensor, p: float, seed: int, stream=None) -> Sample:
     return Sample(x, p, seed, stream)
+
+
+def sample_noalloc(x: torch.Tensor, p: float, seed: int, idx_out: torch.Tensor, val_out: torch.Tensor,
+                   stream=None) -> int:
+    """Kept (index, value) pairs written into the caller's preallocated
+    idx_out (int64) and val_out (x's dtype); returns the number kept.  Raises
+    MachError when the capacity min(len(idx_out), len(val_out)) is too small
+    (the count is in the exception's ``n_kept``).  Nothing is allocated."""
+    lib = load()
+    if not x.is_contiguous():
+        raise ValueError("x must be contiguous")
+    if idx_out.dtype != torch.int64 or val_out.dtype != x.dtype:
+        raise TypeError("idx_out must be int64 and val_out of x's dtype")
+    cap = min(idx_out.numel(), val_out.numel())
+    n = ctypes.c_int64(0)
+    st = lib.mach_sample_noalloc(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), x.dim(), _i64(x.shape),
+                                 float(p), ctypes.c_uint64(seed), ctypes.c_void_p(idx_out.data_ptr()),
+                                 ctypes.c_void_p(val_out.data_ptr()), cap, ctypes.byref(n), _stream(stream))
+    if st != 0:
+        err = MachError("mach_sample_noalloc", st, lib.mach_last_error().decode(errors="replace"))
+        err.n_kept = int(n.value)
+        raise err
+    return int(n.value)
 
 
 def error(x: torch.Tensor, core: torch.Tensor, factors: Sequence[torch.Tensor], stream=None):
