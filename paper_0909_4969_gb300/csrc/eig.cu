@@ -32,89 +32,128 @@ constexpr int kEigSmallMax = 256;
 // b-space helpers: one warp, matrices in shared memory with leading dim kLd.
 // ----------------------------------------------------------------------------
 
-// Cyclic Jacobi (Golub & Van Loan, sym.schur2 rotations; round-robin pair
-// ordering): H <- J^T H J until the off-diagonal mass is below rel_tol of the
-// diagonal, or stalls at the rounding floor.  Qm accumulates J (columns =
-// eigenvectors).  Lane i owns row i for the column updates and column i for
-// the row updates.
-template <typename T>
-__device__ void jacobi_warp(T* H, T* Qm, int n, T rel_tol, int max_sweeps, T* cs, int* pq) {
+// Cyclic Jacobi (Golub & Van Loan, sym.schur2 rotations) in round-robin
+// ("circle") pair order, register resident on one warp.  The matrix is kept
+// in position order: lane a holds row a of H and the positions pair up as
+// (k, NP-1-k) in every round; after each round positions 1..NP-1 shift by
+// one (rows by a shuffle, columns by renaming registers), which walks
+// through the circle pairings with every register index a compile-time
+// constant.  After NP-1 rounds (one sweep) the order is the identity again.
+// Lane i also holds row i of the accumulated rotation Q (columns =
+// eigenvectors, in position order).  Padding to NP (a multiple of 8, <= 32)
+// is zero and stays exactly zero.  H <- J^T H J until the off-diagonal mass
+// is below rel_tol^2 of the diagonal's, or stalls at the rounding floor;
+// the result goes back to H and Q (shared memory, leading dimension kLd).
+template <typename T, int NP>
+__device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int n, T rel_tol, int max_sweeps) {
   const int lane = threadIdx.x & 31;
-  for (int j = 0; j < n; ++j)
-    if (lane < n) Qm[lane * kLd + j] = (lane == j) ? T(1) : T(0);
-  __syncwarp();
-  if (n <= 1) return;
-  const int np = (n + 1) & ~1;
-  const int npairs = np / 2;
+  const bool in_np = lane < NP;
+  const int mate = in_np ? NP - 1 - lane : lane;                       // partner position
+  const int src = lane == 0 || !in_np ? lane : (lane == NP - 1 ? 1 : lane + 1);  // row shift
+  const int pair = lane < NP / 2 ? lane : NP - 1 - lane;
+  const bool is_p = lane < NP / 2;
+  T h[NP], q[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    h[j] = (lane < n && j < n) ? Hs[lane * kLd + j] : T(0);
+    q[j] = lane == j ? T(1) : T(0);
+  }
   T prev_off = T(-1);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = T(0), dia = T(0);
-    if (lane < n)
-      for (int j = 0; j < n; ++j) {
-        const T h = H[lane * kLd + j];
-        if (j == lane) dia += h * h; else off += h * h;
-      }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const T v = h[j] * h[j];
+      if (j == lane) dia += v; else off += v;
+    }
     off = warp_sum(off);
     dia = warp_sum(dia);
     if (off <= rel_tol * rel_tol * dia) break;
     const T floor_rel = sizeof(T) == 8 ? T(1e-12) : T(1e-4);
     if (prev_off >= T(0) && off > T(0.25) * prev_off && off <= floor_rel * floor_rel * dia) break;
     prev_off = off;
-    for (int round = 0; round < np - 1; ++round) {
-      if (lane < npairs) {
-        const int pa = lane, pb = np - 1 - lane;
-        int p = pa == 0 ? 0 : ((pa - 1 + round) % (np - 1)) + 1;
-        int q = pb == 0 ? 0 : ((pb - 1 + round) % (np - 1)) + 1;
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        T c = T(1), s = T(0);
-        if (q < n) {
-          const T hpq = H[p * kLd + q];
-          if (hpq != T(0)) {
-            const T tau = (H[q * kLd + q] - H[p * kLd + p]) / (T(2) * hpq);
-            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-            c = T(1) / sqrt(T(1) + t * t);
-            s = t * c;
-          }
-        }
-        cs[2 * lane] = c;
-        cs[2 * lane + 1] = s;
-        pq[2 * lane] = p;
-        pq[2 * lane + 1] = q < n ? q : -1;
-      }
-      __syncwarp();
-      if (lane < n) {
-        for (int k = 0; k < npairs; ++k) {
-          const int q = pq[2 * k + 1];
-          if (q < 0) continue;
-          const int p = pq[2 * k];
-          const T c = cs[2 * k], s = cs[2 * k + 1];
-          const T hp = H[lane * kLd + p], hq = H[lane * kLd + q];
-          H[lane * kLd + p] = c * hp - s * hq;
-          H[lane * kLd + q] = s * hp + c * hq;
-          const T qp = Qm[lane * kLd + p], qq = Qm[lane * kLd + q];
-          Qm[lane * kLd + p] = c * qp - s * qq;
-          Qm[lane * kLd + q] = s * qp + c * qq;
+#pragma unroll 1
+    for (int round = 0; round < NP - 1; ++round) {
+      // lane k < NP/2 takes (h_pp, h_qq, h_pq) of pair (k, NP-1-k)
+      T pp = T(0), qq = T(0), pq = T(0);
+#pragma unroll
+      for (int k = 0; k < NP / 2; ++k) {
+        const T vpp = __shfl_sync(0xffffffffu, h[k], k);
+        const T vqq = __shfl_sync(0xffffffffu, h[NP - 1 - k], NP - 1 - k);
+        const T vpq = __shfl_sync(0xffffffffu, h[NP - 1 - k], k);
+        if (lane == k) {
+          pp = vpp;
+          qq = vqq;
+          pq = vpq;
         }
       }
-      __syncwarp();
-      if (lane < n) {
-        for (int k = 0; k < npairs; ++k) {
-          const int q = pq[2 * k + 1];
-          if (q < 0) continue;
-          const int p = pq[2 * k];
-          const T c = cs[2 * k], s = cs[2 * k + 1];
-          const T hp = H[p * kLd + lane], hq = H[q * kLd + lane];
-          H[p * kLd + lane] = c * hp - s * hq;
-          H[q * kLd + lane] = s * hp + c * hq;
-        }
+      T c = T(1), sn = T(0);
+      if (pq != T(0)) {
+        const T tau = (qq - pp) / (T(2) * pq);
+        const T at = fabs(tau);
+        const T t = at > T(1e15) ? T(0.5) / tau : (tau >= T(0) ? T(1) : T(-1)) / (at + sqrt(T(1) + tau * tau));
+        c = T(1) / sqrt(T(1) + t * t);
+        sn = t * c;
       }
-      __syncwarp();
+      // H <- H J and Q <- Q J (columns k, NP-1-k of every lane's row)
+#pragma unroll
+      for (int k = 0; k < NP / 2; ++k) {
+        const T ck = __shfl_sync(0xffffffffu, c, k), sk = __shfl_sync(0xffffffffu, sn, k);
+        const T hp = h[k], hq = h[NP - 1 - k];
+        h[k] = ck * hp - sk * hq;
+        h[NP - 1 - k] = sk * hp + ck * hq;
+        const T qp = q[k], qv = q[NP - 1 - k];
+        q[k] = ck * qp - sk * qv;
+        q[NP - 1 - k] = sk * qp + ck * qv;
+      }
+      // H <- J^T H: rows k and NP-1-k, exchanged between the pair's lanes
+      T cm = __shfl_sync(0xffffffffu, c, pair), sm = __shfl_sync(0xffffffffu, sn, pair);
+      if (!in_np) {
+        cm = T(1);
+        sm = T(0);
+      }
+      const T sg = is_p ? -sm : sm;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const T other = __shfl_sync(0xffffffffu, h[j], mate);
+        h[j] = cm * h[j] + sg * other;
+      }
+      // next pairing: position a takes the contents of position src(a)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) h[j] = __shfl_sync(0xffffffffu, h[j], src);
+      const T h1 = h[1], q1 = q[1];
+#pragma unroll
+      for (int j = 1; j < NP - 1; ++j) {
+        h[j] = h[j + 1];
+        q[j] = q[j + 1];
+      }
+      h[NP - 1] = h1;
+      q[NP - 1] = q1;
     }
   }
+  if (lane < n) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (j < n) {
+        Hs[lane * kLd + j] = h[j];
+        Qs[lane * kLd + j] = q[j];
+      }
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ void jacobi_warp(T* H, T* Qm, int n, T rel_tol, int max_sweeps) {
+  if (n <= 8) jacobi_reg<T, 8>(H, Qm, n, rel_tol, max_sweeps);
+  else if (n <= 16) jacobi_reg<T, 16>(H, Qm, n, rel_tol, max_sweeps);
+  else if (n <= 24) jacobi_reg<T, 24>(H, Qm, n, rel_tol, max_sweeps);
+  else jacobi_reg<T, 32>(H, Qm, n, rel_tol, max_sweeps);
+}
+
+// Same for n <= 16 (the final r x r Rayleigh-Ritz; r <= 16).
+__device__ void jacobi_warp_small(double* H, double* Qm, int n, double rel_tol, int max_sweeps) {
+  if (n <= 8) jacobi_reg<double, 8>(H, Qm, n, rel_tol, max_sweeps);
+  else jacobi_reg<double, 16>(H, Qm, n, rel_tol, max_sweeps);
 }
 
 // perm[0..n): indices of the diagonal of H in descending order (ties: lower index first).
@@ -190,7 +229,6 @@ struct BSpace {
   T Q[kB * kLd];    // eigenvectors of H (unsorted columns)
   T S[kB * kLd];    // next-basis transform (or sorted Q)
   T G[kB * kLd];    // scratch
-  T cs[2 * kB];
   int pq[2 * kB];
   int perm[kB];
   T theta[kB];
@@ -199,85 +237,93 @@ struct BSpace {
   int conv;
 };
 
-// Warp 0: Jacobi on H, sort, residual test (needs F unless `check` is false),
-// and, when not converged, S = Q_sorted D R^-1 with R = chol(D Q^T P Q D).
+// All threads of the CTA (blockDim.x threads, b-space matrices in shared
+// memory): warp 0 runs Jacobi on H and sorts; the residual test (needs F
+// unless `check` is false) and, when not converged, S = Q_sorted D R^-1
+// with R = chol(D Q^T P Q D).  The b x b products are spread over the CTA.
 // When converged (or `final_rotation`), S = Q_sorted (Ritz vectors U = V S).
+// *prev (shared) carries the previous residual between iterations.
 template <typename T>
 __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev, bool check, bool final_rotation) {
-  const int lane = threadIdx.x & 31;
-  // FP32: 1e-6 relative off-diagonal is at the arithmetic's resolution for
-  // the Ritz rotation; the sweep cap only binds on a cold start, whose basis
-  // the following iterations refine anyway.
-  jacobi_warp<T>(s.H, s.Q, b, sizeof(T) == 8 ? T(1e-14) : T(1e-6), sizeof(T) == 8 ? 12 : 8, s.cs, s.pq);
-  sort_desc_warp<T>(s.H, b, s.perm);
-  if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
-  // sorted eigenvectors into S
-  for (int j = 0; j < b; ++j)
-    if (lane < b) s.S[lane * kLd + j] = s.Q[lane * kLd + s.perm[j]];
-  __syncwarp();
-  bool conv = false;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 32) {
+    jacobi_warp<T>(s.H, s.Q, b, sizeof(T) == 8 ? T(1e-14) : T(1e-6), sizeof(T) == 8 ? 12 : 8);
+    sort_desc_warp<T>(s.H, b, s.perm);
+    if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
+  }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += blockDim.x) {
+    const int a = e / b, j = e - a * b;
+    s.S[a * kLd + j] = s.Q[a * kLd + s.perm[j]];
+  }
+  __syncthreads();
   if (check) {
-    // res_j^2 = q_j^T F q_j for the leading r Ritz pairs (lane j)
-    double res = 0.0;
-    if (lane < r) {
-      for (int a = 0; a < b; ++a) {
-        T fq = T(0);
-        for (int c = 0; c < b; ++c) fq += s.F[a * kLd + c] * s.S[c * kLd + lane];
-        res += (double)s.S[a * kLd + lane] * (double)fq;
+    // res_j^2 = q_j^T F q_j for the leading r Ritz pairs
+    for (int e = tid; e < b * r; e += blockDim.x) {
+      const int a = e / r, j = e - a * r;
+      T fq = T(0);
+      for (int c = 0; c < b; ++c) fq += s.F[a * kLd + c] * s.S[c * kLd + j];
+      s.G[a * kLd + j] = fq;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double res = 0.0;
+      if (lane < r)
+        for (int a = 0; a < b; ++a) res += (double)s.S[a * kLd + lane] * (double)s.G[a * kLd + lane];
+      res = res > 0.0 ? sqrt(res) : 0.0;
+      double worst = res;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+      const double th0 = fabs((double)s.theta[0]);
+      const double rel = th0 > 0.0 ? worst / th0 : 0.0;
+      const bool floor_hit = rel < 10.0 * tol && rel > 0.5 * (*prev);
+      const bool conv = (th0 == 0.0) || rel <= tol || floor_hit;
+      __syncwarp();
+      if (lane == 0) {
+        s.conv = conv ? 1 : 0;
+        *prev = rel;
       }
     }
-    res = res > 0.0 ? sqrt(res) : 0.0;
-    double worst = res;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-    const double th0 = fabs((double)s.theta[0]);
-    const double rel = th0 > 0.0 ? worst / th0 : 0.0;
-    const bool floor_hit = rel < 10.0 * tol && rel > 0.5 * (*prev);
-    conv = (th0 == 0.0) || rel <= tol || floor_hit;
-    *prev = rel;
+  } else if (tid == 0) {
+    s.conv = 0;
   }
-  if (lane == 0) s.conv = conv ? 1 : 0;
-  if (conv || final_rotation) {
-    __syncwarp();
-    return;
-  }
-  // G = S^T P S (S = sorted Q), then column scaling D and Cholesky
-  for (int j = 0; j < b; ++j) {
-    if (lane < b) {
-      T acc = T(0);
-      for (int c = 0; c < b; ++c) acc += s.P[lane * kLd + c] * s.S[c * kLd + j];
-      s.G[lane * kLd + j] = acc;   // (P S)[lane][j]
-    }
-  }
-  __syncwarp();
-  T row[kB];
-  for (int j = 0; j < b; ++j) {
+  __syncthreads();
+  if (s.conv || final_rotation) return;
+  // G = P S, then F = S^T G (F is free once the residual is taken)
+  for (int e = tid; e < b * b; e += blockDim.x) {
+    const int a = e / b, j = e - a * b;
     T acc = T(0);
-    if (lane < b)
-      for (int a = 0; a < b; ++a) acc += s.S[a * kLd + lane] * s.G[a * kLd + j];
-    row[j] = acc;   // (S^T P S)[lane][j]
+    for (int c = 0; c < b; ++c) acc += s.P[a * kLd + c] * s.S[c * kLd + j];
+    s.G[a * kLd + j] = acc;
   }
-  __syncwarp();
-  for (int j = 0; j < b; ++j)
-    if (lane < b) s.G[lane * kLd + j] = row[j];
-  __syncwarp();
-  col_scale_warp<T>(s.G, b, s.d);
-  // D G D
-  if (lane < b)
-    for (int j = 0; j < b; ++j) s.G[lane * kLd + j] *= s.d[lane] * s.d[j];
-  __syncwarp();
-  chol_warp<T>(s.G, b, s.dead);
-  // S <- S D R^-1 : row `lane` of S D, forward substitution against upper R
-  if (lane < b) {
-    for (int j = 0; j < b; ++j) row[j] = s.S[lane * kLd + j] * s.d[j];
+  __syncthreads();
+  for (int e = tid; e < b * b; e += blockDim.x) {
+    const int a = e / b, j = e - a * b;
+    T acc = T(0);
+    for (int c = 0; c < b; ++c) acc += s.S[c * kLd + a] * s.G[c * kLd + j];
+    s.F[a * kLd + j] = acc;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    col_scale_warp<T>(s.F, b, s.d);
+    if (lane < b)
+      for (int j = 0; j < b; ++j) s.F[lane * kLd + j] *= s.d[lane] * s.d[j];
+    __syncwarp();
+    chol_warp<T>(s.F, b, s.dead);
+  }
+  __syncthreads();
+  // S <- S D R^-1: forward substitution against upper R, one row per thread
+  if (tid < b) {
+    T row[kB];
+    for (int j = 0; j < b; ++j) row[j] = s.S[tid * kLd + j] * s.d[j];
     for (int j = 0; j < b; ++j) {
       T v = row[j];
-      for (int k = 0; k < j; ++k) v -= row[k] * s.G[k * kLd + j];
-      row[j] = s.dead[j] ? T(0) : v / s.G[j * kLd + j];
+      for (int k = 0; k < j; ++k) v -= row[k] * s.F[k * kLd + j];
+      row[j] = s.dead[j] ? T(0) : v / s.F[j * kLd + j];
     }
-    for (int j = 0; j < b; ++j) s.S[lane * kLd + j] = row[j];
+    for (int j = 0; j < b; ++j) s.S[tid * kLd + j] = row[j];
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // ----------------------------------------------------------------------------
@@ -285,29 +331,47 @@ __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev
 // ----------------------------------------------------------------------------
 
 // W[i, :ncols] = C[i, :] V[:, :ncols] for rows i in [i0, i1); warp per RPW
-// rows, lane j per column j of V (coalesced rows of V, broadcast C).
+// rows, lane j per column j of V (coalesced rows of V, broadcast C).  The
+// k loop keeps 8 independent partial sums per row so that 8 loads of C and
+// V are in flight per lane (the operands may live in global memory).
 template <typename T, int RPW>
 __device__ void cv_rows(const T* C, int M, const T* V, int b, T* W, int ncols, int i0, int i1, int warp, int nwarps) {
+  constexpr int KU = 8;
   const int lane = threadIdx.x & 31;
   for (int r0 = i0 + RPW * warp; r0 < i1; r0 += RPW * nwarps) {
     const int nr = min(RPW, i1 - r0);
     const T* crow[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) crow[q] = C + (size_t)(r0 + (q < nr ? q : 0)) * M;
-    T acc[RPW];
+    T acc[RPW][KU];
 #pragma unroll
-    for (int q = 0; q < RPW; ++q) acc[q] = T(0);
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int u = 0; u < KU; ++u) acc[q][u] = T(0);
     if (lane < ncols) {
       const T* vc = V + lane;
-#pragma unroll 4
-      for (int k = 0; k < M; ++k) {
+      int k = 0;
+      for (; k + KU <= M; k += KU) {
+        T v[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u) v[u] = vc[(size_t)(k + u) * b];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+          for (int u = 0; u < KU; ++u) acc[q][u] += crow[q][k + u] * v[u];
+      }
+      for (; k < M; ++k) {
         const T v = vc[(size_t)k * b];
 #pragma unroll
-        for (int q = 0; q < RPW; ++q) acc[q] += crow[q][k] * v;
+        for (int q = 0; q < RPW; ++q) acc[q][0] += crow[q][k] * v;
       }
 #pragma unroll
-      for (int q = 0; q < RPW; ++q)
-        if (q < nr) W[(size_t)(r0 + q) * b + lane] = acc[q];
+      for (int q = 0; q < RPW; ++q) {
+        T t = T(0);
+#pragma unroll
+        for (int u = 0; u < KU; ++u) t += acc[q][u];
+        if (q < nr) W[(size_t)(r0 + q) * b + lane] = t;
+      }
     }
   }
 }
@@ -388,7 +452,7 @@ __device__ void final_rr(const T* U, const T* CU, int M, int b, int r, double* V
         H64[j * kLd + lane] = avg;
       }
     __syncwarp();
-    jacobi_warp<double>(H64, Q64, r, 1e-15, 12, cs64, pq);
+    jacobi_warp_small(H64, Q64, r, 1e-15, 12);
     sort_desc_warp<double>(H64, r, perm);
   }
   __syncthreads();
@@ -480,7 +544,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
   int it = 0;
   bool conv = false;
   for (; it < a.maxit; ++it) {
-    cv_rows<T, 4>(C, M, V, b, W, b, 0, M, warp, kEigWarps);
+    cv_rows<T, 2>(C, M, V, b, W, b, 0, M, warp, kEigWarps);
     __syncthreads();
     grams_rows<T>(V, W, b, 0, M, bs.H, bs.P, kLd);
     __syncthreads();
@@ -488,8 +552,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     __syncthreads();
     grams_rows<T>(U, U, b, 0, M, bs.F, nullptr, kLd);
     __syncthreads();
-    if (threadIdx.x < 32) bspace_step<T>(bs, b, r, a.tol, &prev, true, it + 1 == a.maxit);
-    __syncthreads();
+    bspace_step<T>(bs, b, r, a.tol, &prev, true, it + 1 == a.maxit);
     if (bs.conv || it + 1 == a.maxit) {
       conv = bs.conv != 0;
       apply_rows<T>(V, bs.S, b, b, U, b, 0, M);   // Ritz vectors
@@ -508,7 +571,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
   }
   if (a.basis_out)
     for (int o = threadIdx.x; o < M * b; o += blockDim.x) a.basis_out[o] = U[o];
-  cv_rows<T, 4>(C, M, U, b, W, r, 0, M, warp, kEigWarps);
+  cv_rows<T, 2>(C, M, U, b, W, r, 0, M, warp, kEigWarps);
   __syncthreads();
   final_rr<T>(U, W, M, b, r, a.Vout, a.theta, H64, Q64, cs64, bs.pq, bs.perm);
   if (threadIdx.x == 0 && a.stats) {
@@ -593,11 +656,14 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
           bs.H[j * kLd + lane] = avg;
         }
       __syncwarp();
-      double prev = 1e300;
-      bspace_step<T>(bs, b, r, 0.0, &prev, false, mode == 2);
     }
   }
   __syncthreads();
+  if (mode != 0) {
+    __shared__ double prev;
+    if (threadIdx.x == 0) prev = 1e300;
+    bspace_step<T>(bs, b, r, 0.0, &prev, false, mode == 2);
+  }
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int p = e / b, q = e - (e / b) * b;
     S_out[p * kB + q] = bs.S[p * kLd + q];
