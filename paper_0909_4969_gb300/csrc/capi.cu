@@ -244,7 +244,9 @@ Cyc cyc(int d, int n) {
 // spectrum is crowded near r.  Warm-started HOOI updates use at least 16
 // columns; the cold HOSVD start always uses the full 32.
 int block_size_for(int M, int r, bool cold) {
-  int b = cold ? 32 : std::max(std::max(2 * r, r + 8), 16);
+  // warm starts (previous factor + previous Ritz directions) need few
+  // iterations, so the block carries only a few guard directions past r
+  int b = cold ? 32 : std::max(r + 6, 16);
   b = std::min(b, 32);
   return std::min(b, M);
 }

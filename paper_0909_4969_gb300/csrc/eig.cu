@@ -23,7 +23,6 @@ namespace mach {
 namespace {
 
 constexpr int kEigThreads = 256;
-constexpr int kEigWarps = kEigThreads / 32;
 constexpr int kB = 32;        // maximum block width
 constexpr int kLd = kB + 1;   // padded leading dimension of b x b matrices
 constexpr int kEigSmallMax = 256;
@@ -43,9 +42,9 @@ constexpr int kEigSmallMax = 256;
 // eigenvectors, in position order).  Padding to NP (a multiple of 8, <= 32)
 // is zero and stays exactly zero.  H <- J^T H J until the off-diagonal mass
 // is below rel_tol^2 of the diagonal's, or stalls at the rounding floor;
-// the result goes back to H and Q (shared memory, leading dimension kLd).
+// the result goes back to H and Q (shared memory, leading dimension ldm).
 template <typename T, int NP>
-__device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int n, T rel_tol, int max_sweeps) {
+__device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int ldm, int n, T rel_tol, int max_sweeps) {
   const int lane = threadIdx.x & 31;
   const bool in_np = lane < NP;
   const int mate = in_np ? NP - 1 - lane : lane;                       // partner position
@@ -55,7 +54,7 @@ __device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int n, T rel_tol, int max_
   T h[NP], q[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    h[j] = (lane < n && j < n) ? Hs[lane * kLd + j] : T(0);
+    h[j] = (lane < n && j < n) ? Hs[lane * ldm + j] : T(0);
     q[j] = lane == j ? T(1) : T(0);
   }
   T prev_off = T(-1);
@@ -135,8 +134,8 @@ __device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int n, T rel_tol, int max_
 #pragma unroll
     for (int j = 0; j < NP; ++j)
       if (j < n) {
-        Hs[lane * kLd + j] = h[j];
-        Qs[lane * kLd + j] = q[j];
+        Hs[lane * ldm + j] = h[j];
+        Qs[lane * ldm + j] = q[j];
       }
   }
   __syncwarp();
@@ -144,16 +143,19 @@ __device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int n, T rel_tol, int max_
 
 template <typename T>
 __device__ void jacobi_warp(T* H, T* Qm, int n, T rel_tol, int max_sweeps) {
-  if (n <= 8) jacobi_reg<T, 8>(H, Qm, n, rel_tol, max_sweeps);
-  else if (n <= 16) jacobi_reg<T, 16>(H, Qm, n, rel_tol, max_sweeps);
-  else if (n <= 24) jacobi_reg<T, 24>(H, Qm, n, rel_tol, max_sweeps);
-  else jacobi_reg<T, 32>(H, Qm, n, rel_tol, max_sweeps);
+  if (n <= 8) jacobi_reg<T, 8>(H, Qm, kLd, n, rel_tol, max_sweeps);
+  else if (n <= 12) jacobi_reg<T, 12>(H, Qm, kLd, n, rel_tol, max_sweeps);
+  else if (n <= 16) jacobi_reg<T, 16>(H, Qm, kLd, n, rel_tol, max_sweeps);
+  else if (n <= 20) jacobi_reg<T, 20>(H, Qm, kLd, n, rel_tol, max_sweeps);
+  else if (n <= 24) jacobi_reg<T, 24>(H, Qm, kLd, n, rel_tol, max_sweeps);
+  else jacobi_reg<T, 32>(H, Qm, kLd, n, rel_tol, max_sweeps);
 }
 
-// Same for n <= 16 (the final r x r Rayleigh-Ritz; r <= 16).
-__device__ void jacobi_warp_small(double* H, double* Qm, int n, double rel_tol, int max_sweeps) {
-  if (n <= 8) jacobi_reg<double, 8>(H, Qm, n, rel_tol, max_sweeps);
-  else jacobi_reg<double, 16>(H, Qm, n, rel_tol, max_sweeps);
+// FP64, n <= 16, leading dimension ldm (fallback of the final Rayleigh-Ritz).
+__device__ void jacobi_warp_small(double* H, double* Qm, int ldm, int n, double rel_tol, int max_sweeps) {
+  if (n <= 8) jacobi_reg<double, 8>(H, Qm, ldm, n, rel_tol, max_sweeps);
+  else if (n <= 12) jacobi_reg<double, 12>(H, Qm, ldm, n, rel_tol, max_sweeps);
+  else jacobi_reg<double, 16>(H, Qm, ldm, n, rel_tol, max_sweeps);
 }
 
 // perm[0..n): indices of the diagonal of H in descending order (ties: lower index first).
@@ -229,7 +231,6 @@ struct BSpace {
   T Q[kB * kLd];    // eigenvectors of H (unsorted columns)
   T S[kB * kLd];    // next-basis transform (or sorted Q)
   T G[kB * kLd];    // scratch
-  int pq[2 * kB];
   int perm[kB];
   T theta[kB];
   T d[kB];          // column scaling
@@ -376,37 +377,71 @@ __device__ void cv_rows(const T* C, int M, const T* V, int b, T* W, int ncols, i
   }
 }
 
-// Gram-type sums over rows [i0, i1): H += X^T Y, P += Y^T Y (when P != null).
-// Thread t owns entries t, t + 256, .. of the b x b results.
+// Out[i, j] = A[i, :K] B[:K, j]  (or Sub[i, j] - A[i, :K] B[:K, j] when Sub
+// is given) for i < M, j < nc; all row-major with the given leading
+// dimensions.  Each thread owns a 4 x 4 register tile of Out (16 FMAs per
+// 8 loads); all threads of the CTA share the tiles.
 template <typename T>
-__device__ void grams_rows(const T* X, const T* Y, int b, int i0, int i1, T* Hout, T* Pout, int ldo) {
+__device__ void tile_gemm(const T* A, int lda, const T* B, int ldb, int M, int K, int nc, T* Out, int ldo,
+                          const T* Sub) {
+  const int cg = (nc + 3) >> 2, rg = (M + 3) >> 2;
+  for (int t = threadIdx.x; t < cg * rg; t += blockDim.x) {
+    const int tr = t / cg, tc = t - tr * cg;
+    const int i0 = tr << 2, j0 = tc << 2;
+    const T* a[4];
+    int jj[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = A + (size_t)min(i0 + q, M - 1) * lda;
+      jj[q] = min(j0 + q, nc - 1);
+    }
+    T acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[q][u] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      T av[4], bv[4];
+      const T* brow = B + (size_t)k * ldb;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        av[q] = a[q][k];
+        bv[q] = brow[jj[q]];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[q][u] += av[q] * bv[u];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + q;
+      if (i >= M) break;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u;
+        if (j < nc) Out[(size_t)i * ldo + j] = Sub ? Sub[(size_t)i * ldo + j] - acc[q][u] : acc[q][u];
+      }
+    }
+  }
+}
+
+// Gram-type sums over rows [i0, i1): H = X^T Y, P = Y^T Y (when P != null);
+// X, Y row-major with leading dimension ld.  Thread t owns entries t,
+// t + blockDim.x, .. of the b x b results.
+template <typename T>
+__device__ void grams_rows(const T* X, const T* Y, int ld, int b, int i0, int i1, T* Hout, T* Pout, int ldo) {
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int p = e / b, q = e - (e / b) * b;
     T h = T(0), g = T(0);
     for (int i = i0; i < i1; ++i) {
-      const T yq = Y[(size_t)i * b + q];
-      h += X[(size_t)i * b + p] * yq;
-      if (Pout) g += Y[(size_t)i * b + p] * yq;
+      const T yq = Y[(size_t)i * ld + q];
+      h += X[(size_t)i * ld + p] * yq;
+      if (Pout) g += Y[(size_t)i * ld + p] * yq;
     }
     Hout[p * ldo + q] = h;
     if (Pout) Pout[p * ldo + q] = g;
-  }
-}
-
-// E = W - V H for rows [i0, i1) (H from shared memory, ld kLd).
-template <typename T>
-__device__ void resid_rows(const T* V, const T* W, const T* H, int b, int i0, int i1, T* E) {
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    T vr[kB];
-#pragma unroll
-    for (int k = 0; k < kB; ++k) vr[k] = k < b ? V[(size_t)i * b + k] : T(0);
-    for (int j = 0; j < b; ++j) {
-      T acc = W[(size_t)i * b + j];
-#pragma unroll
-      for (int k = 0; k < kB; ++k)
-        if (k < b) acc -= vr[k] * H[k * kLd + j];
-      E[(size_t)i * b + j] = acc;
-    }
   }
 }
 
@@ -428,45 +463,180 @@ __device__ void apply_rows(const T* X, const T* S, int b, int ncols, T* Out, int
 }
 
 // ----------------------------------------------------------------------------
-// Final FP64 Rayleigh-Ritz of the leading r Ritz vectors U (M x b, first r
-// columns) with CU = C U (first r columns): H64 = U_r^T CU_r (FP64 sums),
-// FP64 Jacobi, Vout = U_r Q64, theta.  One CTA.
+// Final Rayleigh-Ritz of the leading r Ritz vectors in FP64 (r <= 16).
+// Given the projected matrix H = U_r^T C U_r and the Gram G = U_r^T U_r of
+// the Ritz basis (orthonormal and diagonalising up to the b-space
+// arithmetic), the eigenvectors of the pencil (H, G) are refined with the
+// iterative refinement of Ogita and Aishima (Japan J. Indust. Appl. Math.
+// 35, 2018): for the estimate X, S = X^T H X, R = I - X^T G X,
+// lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j R_ij) /
+// (lambda_j - lambda_i) for pairs separated by more than
+// delta = 2 (||offdiag S||_F + max|lambda| ||R||_F), R_ij / 2 otherwise,
+// and X <- X (I + E).  The error is squared by every round, so from a
+// start that is diagonal to FP32 precision two rounds reach FP64
+// precision; when four rounds do not converge, a cyclic FP64 Jacobi on H
+// is used instead.  All threads of the CTA; one thread per entry.
 // ----------------------------------------------------------------------------
-template <typename T>
-__device__ void final_rr(const T* U, const T* CU, int M, int b, int r, double* Vout, double* theta, double* H64,
-                         double* Q64, double* cs64, int* pq, int* perm) {
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int p = e / r, q = e - (e / r) * r;
-    double s = 0.0;
-    for (int i = 0; i < M; ++i) s += (double)U[(size_t)i * b + p] * (double)CU[(size_t)i * b + q];
-    H64[p * kLd + q] = s;
-  }
+constexpr int kRl = kMaxRank + 1;
+struct FinalRR {
+  double H[kMaxRank * kRl], G[kMaxRank * kRl], X[kMaxRank * kRl];
+  double T1[kMaxRank * kRl], T2[kMaxRank * kRl];
+  double lam[kMaxRank];
+  double red[3][kEigThreads / 32];
+  double delta, emax;
+  int perm[kMaxRank];
+};
+
+__device__ void rr_refine(FinalRR& f, int r) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const bool act = tid < r * r;
+  const int i = act ? tid / r : 0, j = act ? tid - (tid / r) * r : 0;
+  if (act) f.X[i * kRl + j] = i == j ? 1.0 : 0.0;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    // symmetrise
-    const int lane = threadIdx.x;
-    if (lane < r)
-      for (int j = lane + 1; j < r; ++j) {
-        const double avg = 0.5 * (H64[lane * kLd + j] + H64[j * kLd + lane]);
-        H64[lane * kLd + j] = avg;
-        H64[j * kLd + lane] = avg;
+  bool ok = false;
+  for (int round = 0; round < 4 && !ok; ++round) {
+    if (act) {
+      double a = 0.0, g = 0.0;
+      for (int k = 0; k < r; ++k) {
+        const double x = f.X[k * kRl + j];
+        a += f.H[i * kRl + k] * x;
+        g += f.G[i * kRl + k] * x;
       }
-    __syncwarp();
-    jacobi_warp_small(H64, Q64, r, 1e-15, 12);
-    sort_desc_warp<double>(H64, r, perm);
+      f.T1[i * kRl + j] = a;   // H X
+      f.T2[i * kRl + j] = g;   // G X
+    }
+    __syncthreads();
+    double sx = 0.0, rx = 0.0;
+    if (act) {
+      for (int k = 0; k < r; ++k) {
+        const double x = f.X[k * kRl + i];
+        sx += x * f.T1[k * kRl + j];
+        rx += x * f.T2[k * kRl + j];
+      }
+      rx = (i == j ? 1.0 : 0.0) - rx;
+    }
+    __syncthreads();
+    if (act) {
+      f.T1[i * kRl + j] = sx;  // S
+      f.T2[i * kRl + j] = rx;  // R
+      if (i == j) f.lam[i] = sx / (1.0 - rx);
+    }
+    double o = (act && i != j) ? sx * sx : 0.0, q = act ? rx * rx : 0.0;
+    o = warp_sum(o);
+    q = warp_sum(q);
+    if (lane == 0) {
+      f.red[0][warp] = o;
+      f.red[1][warp] = q;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double so = 0.0, sr = 0.0, lm = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        so += f.red[0][w];
+        sr += f.red[1][w];
+      }
+      for (int k = 0; k < r; ++k) lm = fmax(lm, fabs(f.lam[k]));
+      f.delta = 2.0 * (sqrt(so) + lm * sqrt(sr));
+    }
+    __syncthreads();
+    double e = 0.0;
+    if (act) {
+      if (i == j) {
+        e = 0.5 * rx;
+      } else {
+        const double li = f.lam[i], lj = f.lam[j];
+        e = fabs(lj - li) > f.delta ? (sx + lj * rx) / (lj - li) : 0.5 * rx;
+      }
+    }
+    double em = act ? fabs(e) : 0.0;
+    if (em != em) em = 1e300;   // NaN: never converged
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) em = fmax(em, __shfl_xor_sync(0xffffffffu, em, d));
+    if (lane == 0) f.red[2][warp] = em;
+    __syncthreads();
+    if (act) f.T1[i * kRl + j] = e;   // E (S no longer needed)
+    if (tid == 0) {
+      double m = 0.0;
+      for (int w = 0; w < nw; ++w) m = fmax(m, f.red[2][w]);
+      f.emax = m;
+    }
+    __syncthreads();
+    double xn = 0.0;
+    if (act) {
+      xn = f.X[i * kRl + j];
+      for (int k = 0; k < r; ++k) xn += f.X[i * kRl + k] * f.T1[k * kRl + j];
+    }
+    __syncthreads();
+    if (act) f.X[i * kRl + j] = xn;
+    // the correction of this round was below 1e-9: the remaining error is
+    // of its square
+    ok = f.emax < 1e-9;
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid < 32) {
+      jacobi_warp_small(f.H, f.X, kRl, r, 1e-15, 12);
+      if (tid < r) f.lam[tid] = f.H[tid * kRl + tid];
+    }
+    __syncthreads();
+  }
+  // descending order of lambda (ties: lower index first)
+  if (tid < r) {
+    const double v = f.lam[tid];
+    int rank = 0;
+    for (int k = 0; k < r; ++k) {
+      const double u = f.lam[k];
+      rank += (u > v) || (u == v && k < tid);
+    }
+    f.perm[rank] = tid;
   }
   __syncthreads();
+}
+
+// Vout (M x r, row-major FP64) = U_r X with the columns in descending
+// order of lambda; theta = the sorted lambda.
+template <typename T>
+__device__ void rr_write(const T* U, int ld, int M, int r, const FinalRR& f, double* Vout, double* theta) {
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    double ur[kMaxRank];
-    for (int k = 0; k < r; ++k) ur[k] = (double)U[(size_t)i * b + k];
+    double u[kMaxRank];
+#pragma unroll
+    for (int k = 0; k < kMaxRank; ++k) u[k] = k < r ? (double)U[(size_t)i * ld + k] : 0.0;
     for (int j = 0; j < r; ++j) {
+      const int pj = f.perm[j];
       double s = 0.0;
-      for (int k = 0; k < r; ++k) s += ur[k] * Q64[k * kLd + perm[j]];
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k)
+        if (k < r) s += u[k] * f.X[k * kRl + pj];
       Vout[(size_t)i * r + j] = s;
     }
   }
-  if (threadIdx.x < r) theta[threadIdx.x] = H64[perm[threadIdx.x] * kLd + perm[threadIdx.x]];
+  if (threadIdx.x < r) theta[threadIdx.x] = f.lam[f.perm[threadIdx.x]];
   __syncthreads();
+}
+
+// General form: H = U_r^T CU_r and G = U_r^T U_r by FP64 sums over the M
+// rows (U, CU row-major with leading dimension ld), then refinement.
+template <typename T>
+__device__ void final_rr(const T* U, const T* CU, int M, int ld, int r, double* Vout, double* theta, FinalRR& f) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int p = e / r, q = e - (e / r) * r;
+    double h = 0.0, g = 0.0;
+    for (int i = 0; i < M; ++i) {
+      const double up = (double)U[(size_t)i * ld + p];
+      h += up * (double)CU[(size_t)i * ld + q];
+      g += up * (double)U[(size_t)i * ld + q];
+    }
+    f.T1[p * kRl + q] = h;
+    f.G[p * kRl + q] = g;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int p = e / r, q = e - (e / r) * r;
+    f.H[p * kRl + q] = 0.5 * (f.T1[p * kRl + q] + f.T1[q * kRl + p]);
+  }
+  __syncthreads();
+  rr_refine(f, r);
+  rr_write<T>(U, ld, M, r, f, Vout, theta);
 }
 
 template <typename T>
@@ -492,29 +662,38 @@ template <typename T>
 __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, int smem_mode) {
   extern __shared__ __align__(16) unsigned char eig_smem[];
   __shared__ BSpace<T> bs;
-  __shared__ double H64[kB * kLd], Q64[kB * kLd], cs64[2 * kB];
+  __shared__ FinalRR frr;
   __shared__ double prev;
   const int M = a.M, b = a.b, r = a.r;
-  const int warp = threadIdx.x >> 5;
+  // shared-memory copies use odd leading dimensions (conflict-free tiles)
+  const int ld = smem_mode >= 1 ? (b | 1) : b;
   T* V = a.V;
   T* W = a.W;
   T* U = a.U;
   const T* C = a.C;
+  int ldc = M;
   if (smem_mode >= 1) {
     V = reinterpret_cast<T*>(eig_smem);
-    W = V + (size_t)M * b;
-    U = W + (size_t)M * b;
-    for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = a.V[o];
+    W = V + (size_t)M * ld;
+    U = W + (size_t)M * ld;
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) {
+      const int i = o / b, j = o - (o / b) * b;
+      V[i * ld + j] = a.V[o];
+    }
   }
   if (smem_mode == 2) {
-    T* Cs = U + (size_t)M * b;
-    for (int o = threadIdx.x; o < M * M; o += blockDim.x) Cs[o] = a.C[o];
+    T* Cs = U + (size_t)M * ld;
+    ldc = M | 1;
+    for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
+      const int i = o / M, k = o - (o / M) * M;
+      Cs[i * ldc + k] = a.C[o];
+    }
     C = Cs;
   }
   if (threadIdx.x == 0) prev = 1e300;
   __syncthreads();
   // orthonormalise the start block: P = V^T V, S from its scaled Cholesky
-  grams_rows<T>(V, V, b, 0, M, bs.P, nullptr, kLd);
+  grams_rows<T>(V, V, ld, b, 0, M, bs.P, nullptr, kLd);
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -536,44 +715,69 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     }
   }
   __syncthreads();
-  apply_rows<T>(V, bs.S, b, b, W, b, 0, M);
+  tile_gemm<T>(V, ld, bs.S, kLd, M, b, b, W, ld, nullptr);
   __syncthreads();
-  for (int o = threadIdx.x; o < M * b; o += blockDim.x) V[o] = W[o];
-  __syncthreads();
+  {
+    T* t = V;
+    V = W;
+    W = t;
+  }
 
   int it = 0;
   bool conv = false;
   for (; it < a.maxit; ++it) {
-    cv_rows<T, 2>(C, M, V, b, W, b, 0, M, warp, kEigWarps);
+    tile_gemm<T>(C, ldc, V, ld, M, M, b, W, ld, nullptr);        // W = C V
     __syncthreads();
-    grams_rows<T>(V, W, b, 0, M, bs.H, bs.P, kLd);
+    grams_rows<T>(V, W, ld, b, 0, M, bs.H, bs.P, kLd);           // H = V^T W, P = W^T W
     __syncthreads();
-    resid_rows<T>(V, W, bs.H, b, 0, M, U);   // U is free here
+    tile_gemm<T>(V, ld, bs.H, kLd, M, b, b, U, ld, W);           // E = W - V H (U is free)
     __syncthreads();
-    grams_rows<T>(U, U, b, 0, M, bs.F, nullptr, kLd);
+    grams_rows<T>(U, U, ld, b, 0, M, bs.F, nullptr, kLd);        // F = E^T E
     __syncthreads();
     bspace_step<T>(bs, b, r, a.tol, &prev, true, it + 1 == a.maxit);
     if (bs.conv || it + 1 == a.maxit) {
       conv = bs.conv != 0;
-      apply_rows<T>(V, bs.S, b, b, U, b, 0, M);   // Ritz vectors
+      tile_gemm<T>(V, ld, bs.S, kLd, M, b, b, U, ld, nullptr);   // Ritz vectors
       __syncthreads();
       break;
     }
-    apply_rows<T>(W, bs.S, b, b, U, b, 0, M);     // next basis (into U, then swap)
+    tile_gemm<T>(W, ld, bs.S, kLd, M, b, b, U, ld, nullptr);     // next basis (into U, then swap)
     __syncthreads();
     T* t = V;
     V = U;
     U = t;
   }
   if (a.maxit <= 0) {
-    for (int o = threadIdx.x; o < M * b; o += blockDim.x) U[o] = V[o];
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) {
+      const int i = o / b, j = o - (o / b) * b;
+      U[i * ld + j] = V[i * ld + j];
+    }
     __syncthreads();
   }
   if (a.basis_out)
-    for (int o = threadIdx.x; o < M * b; o += blockDim.x) a.basis_out[o] = U[o];
-  cv_rows<T, 2>(C, M, U, b, W, r, 0, M, warp, kEigWarps);
-  __syncthreads();
-  final_rr<T>(U, W, M, b, r, a.Vout, a.theta, H64, Q64, cs64, bs.pq, bs.perm);
+    for (int o = threadIdx.x; o < M * b; o += blockDim.x) {
+      const int i = o / b, j = o - (o / b) * b;
+      a.basis_out[o] = U[i * ld + j];
+    }
+  if (a.maxit > 0) {
+    // projected matrix and Gram of U_r = V S_r from the last b-space step:
+    // H_r = (S^T H S)[:r, :r] (the Jacobi-rotated H), G_r = S_r^T S_r
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int p = e / r, q = e - (e / r) * r;
+      const int pp = bs.perm[p], pq = bs.perm[q];
+      frr.H[p * kRl + q] = 0.5 * ((double)bs.H[pp * kLd + pq] + (double)bs.H[pq * kLd + pp]);
+      double g = 0.0;
+      for (int k = 0; k < b; ++k) g += (double)bs.S[k * kLd + p] * (double)bs.S[k * kLd + q];
+      frr.G[p * kRl + q] = g;
+    }
+    __syncthreads();
+    rr_refine(frr, r);
+    rr_write<T>(U, ld, M, r, frr, a.Vout, a.theta);
+  } else {
+    tile_gemm<T>(C, ldc, U, ld, M, M, r, W, ld, nullptr);        // C U_r
+    __syncthreads();
+    final_rr<T>(U, W, M, ld, r, a.Vout, a.theta, frr);
+  }
   if (threadIdx.x == 0 && a.stats) {
     atomicAdd(&a.stats[0], 1ull);
     atomicAdd(&a.stats[1], (unsigned long long)min(it + 1, max(a.maxit, 0)));
@@ -598,14 +802,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) split_grams_kernel(const T* V, const T* W, int M, int b, T* part) {
   const int i0 = blockIdx.x * kRowsPerCta;
   T* h = part + (size_t)blockIdx.x * 2 * b * b;
-  grams_rows<T>(V, W, b, i0, min(M, i0 + kRowsPerCta), h, h + b * b, b);
+  grams_rows<T>(V, W, b, b, i0, min(M, i0 + kRowsPerCta), h, h + b * b, b);
 }
 
 // partial start Gram V^T V of a row block
 template <typename T>
 __global__ void __launch_bounds__(256) split_gram_vv_kernel(const T* V, int M, int b, T* part) {
   const int i0 = blockIdx.x * kRowsPerCta;
-  grams_rows<T>(V, V, b, i0, min(M, i0 + kRowsPerCta), part + (size_t)blockIdx.x * 2 * b * b, nullptr, b);
+  grams_rows<T>(V, V, b, b, i0, min(M, i0 + kRowsPerCta), part + (size_t)blockIdx.x * 2 * b * b, nullptr, b);
 }
 
 // one CTA: reduce partials (fixed order), b-space step; S to global (b x b)
@@ -685,9 +889,8 @@ __global__ void __launch_bounds__(256) split_apply_kernel(const T* X, const T* S
 
 template <typename T>
 __global__ void __launch_bounds__(256) split_final_kernel(EigArgs<T> a, const T* U, const T* CU, int iters) {
-  __shared__ double H64[kB * kLd], Q64[kB * kLd], cs64[2 * kB];
-  __shared__ int pq[2 * kB], perm[kB];
-  final_rr<T>(U, CU, a.M, a.b, a.r, a.Vout, a.theta, H64, Q64, cs64, pq, perm);
+  __shared__ FinalRR frr;
+  final_rr<T>(U, CU, a.M, a.b, a.r, a.Vout, a.theta, frr);
   if (threadIdx.x == 0 && a.stats) {
     atomicAdd(&a.stats[0], 1ull);
     atomicAdd(&a.stats[1], (unsigned long long)iters);
@@ -731,7 +934,7 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
     MACH_CUDA_TRY(cudaGetDevice(&dev));
     MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const size_t budget = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
-    const size_t vwu = (size_t)3 * M * b * sizeof(T), cb = (size_t)M * M * sizeof(T);
+    const size_t vwu = (size_t)3 * M * (b | 1) * sizeof(T), cb = (size_t)M * (M | 1) * sizeof(T);
     int mode = 0;
     size_t bytes = 0;
     if (vwu + cb <= budget) {

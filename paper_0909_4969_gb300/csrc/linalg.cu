@@ -241,44 +241,45 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // deterministic sum of the partials (block order), then Cholesky (thread 0)
-  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+  // deterministic sum of the partials: entry e on warp e mod nw, lane l sums
+  // blocks l, l + 32, .. in order, then a fixed butterfly across the lanes
+  double* G = &wsum[0][0];
+  for (int e = warp; e < rr; e += nw) {
     double t = 0.0;
-    for (unsigned k = 0; k < gridDim.x; ++k) t += ((volatile double*)part)[(size_t)k * rr + e];
-    wsum[0][e] = t;
+    for (unsigned k = lane; k < gridDim.x; k += 32) t += __ldcg(part + (size_t)k * rr + e);
+    t = warp_sum(t);
+    if (lane == 0) G[e] = t;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double R[kMaxRank * kMaxRank];
-  for (int k = 0; k < rr; ++k) R[k] = wsum[0][k];
+  if (warp != 0) return;
+  // upper Cholesky G = R^T R in place (one warp, lane c owns column c)
   for (int j = 0; j < r; ++j) {
-    double djj = R[j * r + j];
-    for (int k = 0; k < j; ++k) djj -= R[k * r + j] * R[k * r + j];
+    double djj = G[j * r + j];
     if (!(djj > 0.0)) {
-      atomicOr(err, DEV_NOTPD);
+      if (lane == 0) atomicOr(err, DEV_NOTPD);
       djj = 1e-300;
     }
     djj = sqrt(djj);
-    R[j * r + j] = djj;
-    for (int c = j + 1; c < r; ++c) {
-      double v = R[j * r + c];
-      for (int k = 0; k < j; ++k) v -= R[k * r + j] * R[k * r + c];
-      R[j * r + c] = v / djj;
-    }
-    for (int c = 0; c < j; ++c) R[j * r + c] = 0.0;
+    __syncwarp();
+    if (lane == j) G[j * r + j] = djj;
+    if (lane > j && lane < r) G[j * r + lane] /= djj;
+    __syncwarp();
+    if (lane > j && lane < r)
+      for (int c = lane; c < r; ++c) G[lane * r + c] -= G[j * r + lane] * G[j * r + c];
+    __syncwarp();
   }
-  // inverse of upper-triangular R
-  double Ri[kMaxRank * kMaxRank];
-  for (int k = 0; k < rr; ++k) Ri[k] = 0.0;
-  for (int j = 0; j < r; ++j) {
-    Ri[j * r + j] = 1.0 / R[j * r + j];
-    for (int i = j - 1; i >= 0; --i) {
-      double v = 0.0;
-      for (int k = i + 1; k <= j; ++k) v += R[i * r + k] * Ri[k * r + j];
-      Ri[i * r + j] = -v / R[i * r + i];
+  // R^-1 (upper): lane j back-substitutes column j
+  double* Ri = &wsum[1][0];
+  if (lane < r) {
+    const int j = lane;
+    for (int i = r - 1; i >= 0; --i) {
+      double v = i == j ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) v -= G[i * r + k] * Ri[k * r + j];
+      Ri[i * r + j] = i > j ? 0.0 : v / G[i * r + i];
     }
   }
-  for (int k = 0; k < rr; ++k) rinv[k] = Ri[k];
+  __syncwarp();
+  for (int k = lane; k < rr; k += 32) rinv[k] = Ri[k];
 }
 
 // A = A64 R^-1: FP64 column-major output (I x r) and the row-major copy in T.
