@@ -51,6 +51,24 @@ def test_large_workload_scaled(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uneven_ranks_many_rows(prec):
+    """Uneven ranks (6, 5, 7) on a 260 x 180 x 220 tensor: rows of ~2e3
+    entries split over several TTM tasks (fix-up reduction) in every mode."""
+    spec = synth.TuckerSpec((260, 180, 220), (6, 5, 7), "gaussian", 0.05, 3, "float32")
+    X, _, _ = synth.tucker_numpy(spec)
+    S, G_o, A_o, G_g, A_g, xd = run_both(X, spec.ranks, 0.05, 11, 6, prec)
+    compare_decomposition(O, X.astype(np.float64), G_o, A_o, G_g, A_g, TOL[prec], prec + " uneven ranks, many rows")
+
+
+def test_long_rows_fp32():
+    """Rows of 6e3 - 1.2e4 entries (tasks split rows mid-fibre), FP32."""
+    spec = synth.TuckerSpec((160, 200, 300), (4, 4, 4), "gaussian", 0.05, 5, "float32")
+    X, _, _ = synth.tucker_numpy(spec)
+    S, G_o, A_o, G_g, A_g, xd = run_both(X, spec.ranks, 0.2, 13, 3, "fp32")
+    compare_decomposition(O, X.astype(np.float64), G_o, A_o, G_g, A_g, TOL["fp32"], "fp32 long rows")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_four_way_scaled(prec):
     spec = synth.TuckerSpec((30, 28, 26, 24), (4, 4, 4, 4), "lognormal_sign", 0.05, 1, "float32")
     X, _, _ = synth.tucker_numpy(spec)
