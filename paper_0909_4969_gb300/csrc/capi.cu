@@ -681,6 +681,7 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.part = w.eig_part.ptr;
   e.stats = h->dscal()->eig_stats;
   e.basis_out = w.basis[n].ptr;
+  e.rr = static_cast<double*>(w.gram64.ptr);
   MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));
   return launch_lsv_finish<T>(static_cast<const T*>(w.Y.ptr), e.Vout, e.theta, I, J, r, jroute,
                               static_cast<double*>(w.A64.ptr), static_cast<double*>(w.gram64.ptr),

@@ -789,12 +789,67 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
 // Split path (large M): fixed iteration count, multi-CTA passes.
 // ----------------------------------------------------------------------------
 constexpr int kRowsPerCta = 32;
-constexpr int kCvRowsPerCta = 8;   // C V: one row per warp, M / 8 CTAs
+// W = C V (first nc columns): 64-row x 32-column output tiles with the k
+// range split over gridDim.y (kCvSplit slices).  Tiles of C (stored
+// transposed, so that a thread's 8 rows at one k are contiguous) and of V
+// are staged in shared memory; thread (ty, tx) owns rows 8 ty .. 8 ty + 7 of
+// column tx.  Slice ks writes its partial tile to P[ks] (M x kB); the
+// slices are summed in ks order by cv_reduce_kernel (deterministic).
+constexpr int kCvRows = 64, kCvK = 32, kCvSplit = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256) split_cv_kernel(const T* C, int M, const T* V, int b, T* W, int ncols) {
-  const int i0 = blockIdx.x * kCvRowsPerCta;
-  cv_rows<T, 1>(C, M, V, b, W, ncols, i0, min(M, i0 + kCvRowsPerCta), threadIdx.x >> 5, 8);
+__global__ void __launch_bounds__(256) cv_tiled_kernel(const T* __restrict__ C, int M, const T* __restrict__ V, int b,
+                                                       int nc, T* __restrict__ P) {
+  __shared__ __align__(16) T Ct[kCvK][kCvRows + 16 / sizeof(T)];
+  __shared__ T Vs[kCvK][kB + 1];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int r0 = blockIdx.x * kCvRows;
+  const int kper = (M + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int k0 = blockIdx.y * kper, k1 = min(M, k0 + kper);
+  T acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = T(0);
+  for (int kc = k0; kc < k1; kc += kCvK) {
+#pragma unroll
+    for (int u = 0; u < kCvRows * kCvK / 256; ++u) {
+      const int e = tid + 256 * u;
+      const int rr = e / kCvK, kk = e - (e / kCvK) * kCvK;
+      const int gi = r0 + rr, gk = kc + kk;
+      Ct[kk][rr] = (gi < M && gk < k1) ? C[(size_t)gi * M + gk] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kCvK * 32 / 256; ++u) {
+      const int e = tid + 256 * u;
+      const int kk = e >> 5, j = e & 31;
+      const int gk = kc + kk;
+      Vs[kk][j] = (gk < k1 && j < nc) ? V[(size_t)gk * b + j] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kCvK; ++kk) {
+      const T v = Vs[kk][tx];
+      const T* c = &Ct[kk][ty * 8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += c[q] * v;
+    }
+    __syncthreads();
+  }
+  T* Pk = P + (size_t)blockIdx.y * M * kB;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = r0 + ty * 8 + q;
+    if (i < M && tx < nc) Pk[(size_t)i * kB + tx] = acc[q];
+  }
+}
+
+template <typename T>
+__global__ void cv_reduce_kernel(const T* __restrict__ P, int nsplit, int M, int nc, T* __restrict__ W, int ldw) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= M * nc) return;
+  const int i = o / nc, j = o - (o / nc) * nc;
+  T s = T(0);
+  for (int k = 0; k < nsplit; ++k) s += P[(size_t)k * M * kB + (size_t)i * kB + j];
+  W[(size_t)i * ldw + j] = s;
 }
 
 // partial Grams of a row block: part[blk][0] = V^T W, part[blk][1] = W^T W
@@ -815,7 +870,7 @@ __global__ void __launch_bounds__(256) split_gram_vv_kernel(const T* V, int M, i
 // one CTA: reduce partials (fixed order), b-space step; S to global (b x b)
 template <typename T>
 __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nblk, int b, int r, int mode,
-                                                           T* S_out) {
+                                                           T* S_out, double* rr_out) {
   // mode 0: start block orthonormalisation (part holds V^T V)
   // mode 1: iteration (next basis); mode 2: final (Ritz rotation)
   __shared__ BSpace<T> bs;
@@ -872,6 +927,55 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
     const int p = e / b, q = e - (e / b) * b;
     S_out[p * kB + q] = bs.S[p * kLd + q];
   }
+  if (mode == 2) {
+    // final FP64 Rayleigh-Ritz of U_r = V S_r from the b-space quantities:
+    // H_r = (S^T H S)[:r, :r] (the Jacobi-rotated H), G_r = S_r^T S_r
+    __shared__ FinalRR frr;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int p = e / r, q = e - (e / r) * r;
+      const int pp = bs.perm[p], pq = bs.perm[q];
+      frr.H[p * kRl + q] = 0.5 * ((double)bs.H[pp * kLd + pq] + (double)bs.H[pq * kLd + pp]);
+      double g = 0.0;
+      for (int k = 0; k < b; ++k) g += (double)bs.S[k * kLd + p] * (double)bs.S[k * kLd + q];
+      frr.G[p * kRl + q] = g;
+    }
+    __syncthreads();
+    rr_refine(frr, r);
+    // rr_out: X (r x r, columns in descending order of lambda), then lambda
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int k = e / r, j = e - (e / r) * r;
+      rr_out[e] = frr.X[k * kRl + frr.perm[j]];
+    }
+    if (threadIdx.x < r) rr_out[r * r + threadIdx.x] = frr.lam[frr.perm[threadIdx.x]];
+  }
+}
+
+// Vout = U_r X (FP64, M x r row-major) and theta from rr_out; counts the solve.
+template <typename T>
+__global__ void split_vout_kernel(const T* __restrict__ U, int M, int b, int r, const double* __restrict__ rr_out,
+                                  double* __restrict__ Vout, double* __restrict__ theta,
+                                  unsigned long long* stats, int iters) {
+  __shared__ double X[kMaxRank * kMaxRank];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) X[e] = rr_out[e];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    double u[kMaxRank];
+#pragma unroll
+    for (int k = 0; k < kMaxRank; ++k) u[k] = k < r ? (double)U[(size_t)i * b + k] : 0.0;
+    for (int j = 0; j < r; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < kMaxRank; ++k)
+        if (k < r) s += u[k] * X[k * r + j];
+      Vout[(size_t)i * r + j] = s;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < r) theta[threadIdx.x] = rr_out[r * r + threadIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && stats) {
+    atomicAdd(&stats[0], 1ull);
+    atomicAdd(&stats[1], (unsigned long long)iters);
+  }
 }
 
 // Out = X S (rows of the CTA's block), S from global (b x b, ld kB)
@@ -887,15 +991,6 @@ __global__ void __launch_bounds__(256) split_apply_kernel(const T* X, const T* S
   apply_rows<T>(X, Ss, b, b, Out, b, i0, min(M, i0 + kRowsPerCta));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) split_final_kernel(EigArgs<T> a, const T* U, const T* CU, int iters) {
-  __shared__ FinalRR frr;
-  final_rr<T>(U, CU, a.M, a.b, a.r, a.Vout, a.theta, frr);
-  if (threadIdx.x == 0 && a.stats) {
-    atomicAdd(&a.stats[0], 1ull);
-    atomicAdd(&a.stats[1], (unsigned long long)iters);
-  }
-}
 
 template <typename T>
 __global__ void copy_kernel(const T* src, T* dst, int64_t n) {
@@ -907,7 +1002,11 @@ __global__ void copy_kernel(const T* src, T* dst, int64_t n) {
 
 int eig_split_threshold() { return kEigSmallMax; }
 
-size_t eig_part_elems(int M) { return (size_t)ceil_div(M, kRowsPerCta) * 2 * kB * kB + kB * kB; }
+// split-path scratch: per-row-block partial Grams, the b x b transform S,
+// and the k-split partial tiles of C V
+size_t eig_part_elems(int M) {
+  return (size_t)ceil_div(M, kRowsPerCta) * 2 * kB * kB + kB * kB + (size_t)kCvSplit * M * kB;
+}
 
 template <typename T>
 mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
@@ -953,24 +1052,29 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
   const int nblk = (int)ceil_div(M, kRowsPerCta);
   T* part = a.part;
   T* S = part + (size_t)nblk * 2 * b * b;
+  T* cvp = S + kB * kB;
   T* V = a.V;
   T* W = a.W;
   T* U = a.U;
+  const dim3 cv_grid((unsigned)ceil_div(M, kCvRows), kCvSplit);
+  const unsigned red_grid = (unsigned)ceil_div((int64_t)M * b, 256);
   split_gram_vv_kernel<T><<<nblk, 256, 0, st>>>(V, M, b, part);
   MACH_LAUNCH_CHECK();
-  split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, 0, S);
+  split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, 0, S, e.rr);
   MACH_LAUNCH_CHECK();
   split_apply_kernel<T><<<nblk, 256, 0, st>>>(V, S, M, b, W);
   MACH_LAUNCH_CHECK();
   std::swap(V, W);
   const int iters = std::max(1, e.maxit);
   for (int it = 0; it < iters; ++it) {
-    split_cv_kernel<T><<<(unsigned)ceil_div(M, kCvRowsPerCta), 256, 0, st>>>(C, M, V, b, W, b);
+    cv_tiled_kernel<T><<<cv_grid, 256, 0, st>>>(C, M, V, b, b, cvp);
+    MACH_LAUNCH_CHECK();
+    cv_reduce_kernel<T><<<red_grid, 256, 0, st>>>(cvp, kCvSplit, M, b, W, b);
     MACH_LAUNCH_CHECK();
     split_grams_kernel<T><<<nblk, 256, 0, st>>>(V, W, M, b, part);
     MACH_LAUNCH_CHECK();
     const bool last = it + 1 == iters;
-    split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, last ? 2 : 1, S);
+    split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, last ? 2 : 1, S, e.rr);
     MACH_LAUNCH_CHECK();
     if (last) {
       split_apply_kernel<T><<<nblk, 256, 0, st>>>(V, S, M, b, U);   // Ritz vectors
@@ -986,9 +1090,8 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
         U, a.basis_out, (int64_t)M * b);
     MACH_LAUNCH_CHECK();
   }
-  split_cv_kernel<T><<<(unsigned)ceil_div(M, kCvRowsPerCta), 256, 0, st>>>(C, M, U, b, W, e.r);
-  MACH_LAUNCH_CHECK();
-  split_final_kernel<T><<<1, 256, 0, st>>>(a, U, W, iters);
+  split_vout_kernel<T><<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(U, M, b, e.r, e.rr, a.Vout, a.theta, a.stats,
+                                                                   iters);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }

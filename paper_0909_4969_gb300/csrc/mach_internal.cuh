@@ -326,6 +326,7 @@ struct EigLaunch {
   void* part;                  // >= eig_part_elems(M) elements of T (split path)
   unsigned long long* stats;   // device counters: calls, iterations, unconverged
   void* basis_out;             // M x b T: final Ritz block, or null
+  double* rr;                  // >= kMaxRank * (kMaxRank + 1) doubles (split path)
 };
 int eig_split_threshold();
 size_t eig_part_elems(int M);
