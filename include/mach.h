@@ -220,6 +220,61 @@ mach_status mach_error(const void* x_dev, mach_dtype dtype, int d, const int64_t
                        double* rel_err, double* x_norm, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Served decompositions of tensor streams (the monitoring setting of
+ * Section 1 and Section 4: windows of a stream arrive over time).  Each
+ * request is one mach_sample + mach_hooi (Algorithm 2) + mach_error of one
+ * window.  Windows of one stream warm-start HOOI from the previous window's
+ * factors, which the server keeps on the device; a window whose shape or
+ * ranks differ from its stream's state (a resized window) starts cold from
+ * the HOSVD and leaves that state as it was.
+ *
+ * Continuous batching: `max_slots` worker slots, each with its own CUDA
+ * stream.  A request is admitted as soon as a slot is free, its estimated
+ * device memory fits in what remains of `hbm_budget_bytes`, and no earlier
+ * request of the same stream is pending or running; admitted requests run
+ * concurrently, later ones are admitted as slots and memory free up.
+ *
+ * mach_server_create  budget in bytes (> 0), 1 <= max_slots <= 64, on the
+ *                     current device.  *srv receives the server handle.
+ * mach_submit         queues one window.  x_dev (device, C order, 16-B
+ *                     aligned) stays owned by the caller and must stay valid
+ *                     and unchanged until mach_poll reports it done.  Ranks
+ *                     1 <= r_k <= min(I_k, 16).  *ticket identifies the
+ *                     request.  Errors: MACH_EINVAL (arguments),
+ *                     MACH_ENOMEM_BUDGET (the window can never fit the
+ *                     budget), MACH_EAGAIN (queue full: retry), MACH_EBUSY
+ *                     (server shutting down).
+ * mach_poll           non-blocking.  Not finished: *done = 0, MACH_EAGAIN.
+ *                     Finished: *done = 1, the request's status is
+ *                     returned and, on MACH_OK, the core (prod(r_k) FP64, C
+ *                     order), the factors (FP64 column-major I_k x r_k, one
+ *                     host pointer per mode) and the relative error of
+ *                     Section 4 against the window are copied into the
+ *                     caller's host buffers (any may be NULL).  The ticket
+ *                     is released by that call.
+ * mach_server_stats   completed requests, p50 / p99 of submit-to-done
+ *                     latency (ms, host clock), the most requests ever in
+ *                     flight at once, and the budget in use.  NULL outputs
+ *                     are skipped.
+ * mach_server_destroy drops requests not yet admitted, waits for the ones
+ *                     running, and frees the server and the streams' state.
+ * mach_request_bytes  the device memory the server reserves for one such
+ *                     request (what admission compares with the budget).
+ * Calls on one server may come from any host thread.
+ */
+mach_status mach_server_create(size_t hbm_budget_bytes, int max_slots, void** srv);
+mach_status mach_submit(void* srv, int64_t stream_id, const void* x_dev, mach_dtype dtype, int d,
+                        const int64_t* dims, const int* ranks, double p, uint64_t seed, int sweeps,
+                        mach_prec prec, int64_t* ticket);
+mach_status mach_poll(void* srv, int64_t ticket, int* done, double* core_host,
+                      double* const* factors_host, double* err_out);
+mach_status mach_server_stats(void* srv, int64_t* completed, double* p50_ms, double* p99_ms,
+                              int* max_in_flight, size_t* budget_in_use);
+mach_status mach_server_destroy(void* srv);
+mach_status mach_request_bytes(mach_dtype dtype, int d, const int64_t* dims, const int* ranks, double p,
+                               mach_prec prec, size_t* bytes);
+
+/* ---------------------------------------------------------------------------
  * Profiling (for measurement harnesses).  While enabled, libmach records a
  * CUDA event pair on the launching stream around every launch of the kernel
  * classes below, together with that launch's algorithmic byte count.

@@ -1043,7 +1043,7 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
       mode = 1;
       bytes = vwu;
     }
-    MACH_CUDA_TRY(cudaFuncSetAttribute(eig_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    MACH_TRY(allow_max_dyn_smem(eig_fused_kernel<T>));
     eig_fused_kernel<T><<<1, kEigThreads, bytes, st>>>(a, mode);
     MACH_LAUNCH_CHECK();
     return MACH_OK;

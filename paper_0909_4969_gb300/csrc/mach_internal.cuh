@@ -226,6 +226,21 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   return v;
 }
 
+// Raise a kernel's dynamic shared-memory limit to the most it may use on
+// this device.  The value is the same on every call, so launches from
+// several host threads never lower the limit under one another.
+template <typename F>
+inline mach_status allow_max_dyn_smem(F kern) {
+  cudaFuncAttributes fa;
+  MACH_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, optin = 0;
+  MACH_CUDA_TRY(cudaGetDevice(&dev));
+  MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  MACH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes));
+  return MACH_OK;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -316,7 +316,7 @@ mach_status launch_sampler_t(const void* x, int64_t n, uint64_t seed, uint64_t T
   MACH_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)(num_tiles + 1) * sizeof(unsigned long long), st));
   MACH_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));
   const size_t smem = kSampStages * C::kStageBytes;
-  MACH_CUDA_TRY(cudaFuncSetAttribute(sample_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MACH_TRY(allow_max_dyn_smem(sample_kernel<V>));
   int per_sm = 0;
   MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<V>, kSampThreads, smem));
   if (per_sm < 1) per_sm = 1;

@@ -239,9 +239,8 @@ mach_status counting_sort(const int64_t* idx, const V* val, int64_t K, const int
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
   const size_t smem = (size_t)wpb * nbins * 4;
-  MACH_CUDA_TRY(cudaFuncSetAttribute(cs_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  MACH_CUDA_TRY(
-      cudaFuncSetAttribute(cs_scatter_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MACH_TRY(allow_max_dyn_smem(cs_hist_kernel));
+  MACH_TRY(allow_max_dyn_smem(cs_scatter_kernel<V>));
   const unsigned grid = (unsigned)ceil_div(nwt, wpb);
   cs_hist_kernel<<<grid, 32 * wpb, smem, st>>>(idx, d_count, dec, mode, nbins, nwt, counts);
   MACH_LAUNCH_CHECK();

@@ -363,7 +363,7 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   a.mid0_bytes_staged = D >= 3 ? take((size_t)L.I_mid0 * L.r_mid0) : 0u;
   a.mid1_bytes_staged = D >= 4 ? take((size_t)L.I_mid1 * L.r_mid1) : 0u;
   const size_t smem = (size_t)a.leaf_bytes_staged + a.mid0_bytes_staged + a.mid1_bytes_staged + warp_bytes;
-  MACH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MACH_TRY(allow_max_dyn_smem(kern));
   int per_sm = 0;
   MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kW, smem));
   if (per_sm < 1) per_sm = 1;

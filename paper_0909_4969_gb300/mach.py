@@ -47,6 +47,16 @@ SIGNATURES = {
     "mach_core": (ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_pp, ctypes.c_void_p, ctypes.c_void_p]),
     "mach_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, _c_intp, _c_pp,
                                   ctypes.c_void_p, _c_dblp, _c_dblp, ctypes.c_void_p]),
+    "mach_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "mach_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                   _c_i64p, _c_intp, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                   _c_i64p]),
+    "mach_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _c_intp, ctypes.c_void_p, _c_pp, _c_dblp]),
+    "mach_server_stats": (ctypes.c_int, [ctypes.c_void_p, _c_i64p, _c_dblp, _c_dblp, _c_intp,
+                                         ctypes.POINTER(ctypes.c_size_t)]),
+    "mach_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "mach_request_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _c_i64p, _c_intp, ctypes.c_double, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
     "mach_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mach_profile_query": (ctypes.c_int, [ctypes.c_int, _c_dblp, _c_i64p, _c_dblp]),
     "mach_launch_count": (ctypes.c_int64, []),
@@ -253,6 +263,82 @@ def error(x: torch.Tensor, core: torch.Tensor, factors: Sequence[torch.Tensor], 
                                         ctypes.c_void_p(core.contiguous().data_ptr()), ctypes.byref(rel),
                                         ctypes.byref(xn), _stream(stream)))
     return float(rel.value), float(xn.value)
+
+
+def request_bytes(shape, ranks, p: float, dtype=torch.float32, prec: str = "fp32") -> int:
+    """Device memory the server reserves for one request of this shape."""
+    lib = load()
+    out = ctypes.c_size_t()
+    code = MACH_F32 if dtype == torch.float32 else MACH_F64
+    _check("mach_request_bytes", lib.mach_request_bytes(code, len(shape), _i64(shape), _int(ranks), float(p),
+                                                        PREC[prec], ctypes.byref(out)))
+    return int(out.value)
+
+
+class Server:
+    """Served decompositions of tensor streams (continuous batching over
+    `slots` worker streams within an HBM budget); see include/mach.h."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check("mach_server_create", lib.mach_server_create(int(hbm_budget_bytes), int(slots), ctypes.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, stream_id: int, x: torch.Tensor, ranks: Sequence[int], p: float, seed: int, sweeps: int,
+               prec: str = "fp32") -> int:
+        """Queue one window; x (device, contiguous) must stay alive until polled done."""
+        lib = load()
+        if not x.is_contiguous():
+            raise ValueError("x must be contiguous")
+        t = ctypes.c_int64()
+        _check("mach_submit", lib.mach_submit(self._h, int(stream_id), ctypes.c_void_p(x.data_ptr()),
+                                              _dtype_code(x), x.dim(), _i64(x.shape), _int(ranks), float(p),
+                                              ctypes.c_uint64(seed), int(sweeps), PREC[prec], ctypes.byref(t)))
+        self._shapes[t.value] = (tuple(int(v) for v in x.shape), tuple(int(r) for r in ranks))
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running; then (core, [factors], rel_err) as float64 numpy arrays."""
+        import numpy as np
+        lib = load()
+        dims, ranks = self._shapes[ticket]
+        core = np.empty(ranks, dtype=np.float64)
+        facs = [np.empty((r, i), dtype=np.float64) for i, r in zip(dims, ranks)]   # column-major I x r
+        ptrs = (ctypes.c_void_p * len(facs))(*[f.ctypes.data for f in facs])
+        done = ctypes.c_int()
+        err = ctypes.c_double()
+        st = lib.mach_poll(self._h, int(ticket), ctypes.byref(done), ctypes.c_void_p(core.ctypes.data),
+                           ctypes.cast(ptrs, _c_pp), ctypes.byref(err))
+        if not done.value:
+            return None
+        del self._shapes[ticket]
+        _check("mach_poll", st)
+        return core, [f.T for f in facs], float(err.value)
+
+    def stats(self) -> dict:
+        lib = load()
+        n = ctypes.c_int64()
+        p50 = ctypes.c_double()
+        p99 = ctypes.c_double()
+        mx = ctypes.c_int()
+        used = ctypes.c_size_t()
+        _check("mach_server_stats", lib.mach_server_stats(self._h, ctypes.byref(n), ctypes.byref(p50),
+                                                          ctypes.byref(p99), ctypes.byref(mx), ctypes.byref(used)))
+        return {"completed": n.value, "p50_ms": p50.value, "p99_ms": p99.value, "max_in_flight": mx.value,
+                "budget_in_use": used.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mach_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:
