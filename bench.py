@@ -37,7 +37,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mach", choices=["mach", "reference"])
-    ap.add_argument("--workload", default="large_fp32", choices=["large_fp32", "plain_fp64"])
+    ap.add_argument("--workload", default="large_fp32", choices=["large_fp32", "plain_fp64", "served", "batched"])
+    ap.add_argument("--requests", type=int, default=400, help="served: requests in the timed run")
+    ap.add_argument("--slots", type=int, default=8, help="served / batched: concurrent slots")
+    ap.add_argument("--budget-gb", type=float, default=48.0, help="served / batched: HBM budget")
+    ap.add_argument("--batch", type=int, default=512, help="batched: number of tensors")
     ap.add_argument("--prec", default=None, help="fp32 | fp64 (default: the workload's)")
     ap.add_argument("--scale", type=int, default=1000, help="edge of the large workload (1000 = full size)")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -203,6 +207,133 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# served stream and batched windows (through mach_server_* / mach_submit / mach_poll)
+# ----------------------------------------------------------------------------
+def _drain(srv, tickets):
+    errs = []
+    pending = list(tickets)
+    while pending:
+        rest = []
+        for t in pending:
+            r = srv.poll(t)
+            if r is None:
+                rest.append(t)
+            else:
+                errs.append(r[2])
+        pending = rest
+        if pending:
+            time.sleep(0.0005)
+    return errs
+
+
+def run_served(args):
+    """64 streams of 200 x 16 x 512 FP32 windows rotating by 0.01 rad per
+    window, Poisson arrivals at 2000 windows/s, 10% of the requests resized to
+    1000 x 32 x 4096 (cold start); p = 0.1, ranks (4, 4, 8), 3 warm sweeps.
+    Windows come from a pre-generated device pool (4 per stream, 2 resized)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_0909_4969_gb300 import mach, synth
+    mach.load()
+    n_streams, pool_w = 64, 4
+    small, big = (200, 16, 512), (1000, 32, 4096)
+    ranks, p, sweeps = (4, 4, 8), 0.1, 3
+    prec = args.prec or "fp32"
+    gens = [synth.StreamStateTorch(s, small, ranks, seed=1) for s in range(n_streams)]
+    pool = [[g.next_window(0.01, 0.05) for _ in range(pool_w)] for g in gens]
+    bigs = [synth.tucker_torch(synth.TuckerSpec(big, ranks, "gaussian", 0.05, 100 + k, "float32"))[0]
+            for k in range(2)]
+    torch.cuda.synchronize()
+
+    def one_run(n, seed):
+        sched = synth.served_schedule(n, n_streams, 2000.0, 0.10, seed, small, big)
+        srv = mach.Server(int(args.budget_gb * 2 ** 30), args.slots)
+        tickets = []
+        t0 = time.perf_counter()
+        for req in sched:
+            delay = t0 + req.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            x = bigs[req.window % 2] if req.resized else pool[req.stream][req.window % pool_w]
+            tickets.append(srv.submit(req.stream, x, ranks, p, req.seed, sweeps, prec))
+        errs = _drain(srv, tickets)
+        t1 = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        return n / (t1 - t0), st, errs, t1 - t0, sum(r.resized for r in sched)
+
+    one_run(max(32, 16 * args.warmup), 12345)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    value, st, errs, wall, n_big = one_run(args.requests, 7)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": 1, "steps": args.requests,
+            "warmup": max(32, 16 * args.warmup), "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "served_stream_64x200x16x512", "streams": n_streams, "window": list(small),
+                       "resized_window": list(big), "resize_frac": 0.10, "rate_hz": 2000.0, "p": p,
+                       "ranks": list(ranks), "sweeps": sweeps, "warm_start": True, "slots": args.slots,
+                       "budget_gb": args.budget_gb, "requests": args.requests, "resized_requests": n_big,
+                       "prec": prec},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_in_flight": st["max_in_flight"],
+            "wall_s": wall, "rel_err_median": statistics.median(errs), "rel_err_max": max(errs),
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
+def run_batched(args):
+    """512 independent FP32 tensors of uneven sizes (hosts U{50..400}, types
+    U{8..32}, timeticks log-uniform 64..2048), rank (4, 4, 8), 10% noise,
+    p = 0.1, 10 sweeps: all submitted at once to the server (continuous
+    batching over `slots` streams), against the plain FP64 form (one
+    decomposition at a time, FP64 sweeps) on the same tensors."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_0909_4969_gb300 import mach, synth
+    mach.load()
+    ws = synth.config_batched(args.batch)
+    xs = [synth.tucker_torch(w.spec)[0] for w in ws]
+    torch.cuda.synchronize()
+    ranks = (4, 4, 8)
+    prec = args.prec or "fp32"
+
+    def run(pr, slots, items):
+        srv = mach.Server(int(args.budget_gb * 2 ** 30), slots)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(b, x, ranks, 0.1, b, 10, pr) for b, x in items]
+        errs = _drain(srv, tickets)
+        t1 = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        return len(items) / (t1 - t0), st, errs
+
+    items = list(enumerate(xs))
+    run(prec, args.slots, items[:32])
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    value, st, errs = run(prec, args.slots, items)
+    clk = clocks.stop()
+    plain, st64, errs64 = run("fp64", 1, items)
+    line = {"metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": 1, "steps": len(items),
+            "warmup": 32, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "batched_%d_uneven" % len(items), "ranks": list(ranks), "p": 0.1, "sweeps": 10,
+                       "noise": 0.10, "slots": args.slots, "budget_gb": args.budget_gb, "prec": prec,
+                       "total_input_gb": sum(x.numel() * 4 for x in xs) / 1e9},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_in_flight": st["max_in_flight"],
+            "rel_err_median": statistics.median(errs), "rel_err_max": max(errs),
+            "plain_fp64": {"value": plain, "unit": "decompositions/s", "slots": 1,
+                           "rel_err_median": statistics.median(errs64), "rel_err_max": max(errs64)},
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def config_dict(w, prec):
     return {"workload": w.name, "dims": list(w.spec.dims), "ranks": list(w.spec.ranks), "p": w.p,
             "sweeps": w.sweeps, "noise": w.spec.noise, "core": w.spec.core, "input_dtype": w.spec.dtype,
@@ -217,6 +348,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "served":
+        return run_served(args)
+    if args.workload == "batched":
+        return run_batched(args)
     import torch
     import torch.distributed as dist
 

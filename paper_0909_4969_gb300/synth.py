@@ -243,6 +243,31 @@ class StreamState:
         return np.ascontiguousarray((X + E).astype(dtype))
 
 
+class StreamStateTorch:
+    """Device variant of StreamState for large pools of windows: the small
+    factors rotate on the host (same rotation as StreamState), the window is
+    expanded and noised on the device."""
+
+    def __init__(self, stream: int, dims, ranks=(4, 4, 8), seed: int = 0, device="cuda"):
+        self.host = StreamState(stream, dims, ranks, seed)
+        self.device = device
+        self.gen = torch.Generator(device=device)
+        self.gen.manual_seed(seed * 7919 + stream + 1)
+
+    def next_window(self, theta: float = 0.01, noise: float = 0.05, dtype=None):
+        h = self.host
+        h.Us = [rotate_subspace(U, theta, h.rng) for U in h.Us]
+        d = len(h.dims)
+        letters, upper = "abcdefgh", "ABCDEFGH"
+        expr = letters[:d] + "," + ",".join(upper[k] + letters[k] for k in range(d)) + "->" + upper[:d]
+        G = torch.from_numpy(h.G).to(self.device)
+        Us = [torch.from_numpy(np.ascontiguousarray(U)).to(self.device) for U in h.Us]
+        X = torch.einsum(expr, G, *Us)
+        E = torch.randn(X.shape, generator=self.gen, device=self.device, dtype=torch.float64)
+        E *= noise * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(E)
+        return (X + E).to(dtype or torch.float32).contiguous()
+
+
 def tucker_for_dims(dims, ranks, noise: float, seed: int, dtype="float32", core="gaussian"):
     """Convenience: one seeded Tucker tensor of the given dims (numpy)."""
     X, _, _ = tucker_numpy(TuckerSpec(tuple(dims), tuple(ranks), core, noise, seed, dtype))
