@@ -55,9 +55,11 @@ typedef enum mach_dtype { MACH_F32 = 0, MACH_F64 = 1 } mach_dtype;
 /* Arithmetic of the HOOI sweep.  FP64: every contraction, Gram, eigensolve
  * and QR in FP64.  FP32: tensor-times-matrix chain and Gram in FP32 with FP32
  * accumulation; the R x R eigensolve and the QR re-orthonormalisation in
- * FP64.  BF16_REFINE: sampled values stored in BF16, chain in FP32
- * accumulation, followed by one FP32 subspace-iteration refinement sweep; the
- * small eigensolve and QR in FP64. */
+ * FP64.  BF16_REFINE: the requested sweeps read BF16 copies of the sampled
+ * values (chain in FP32 accumulation), then three more sweeps with the input
+ * values refine the factors (subspace iteration from the BF16 solution; the
+ * core is formed from the input values); the small eigensolve and QR in
+ * FP64. */
 typedef enum mach_prec {
   MACH_PREC_FP64 = 0,
   MACH_PREC_FP32 = 1,

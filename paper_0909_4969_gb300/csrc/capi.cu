@@ -126,6 +126,7 @@ struct SampleScalars {
 struct ModeCsf {
   DevBuf idx;        // mode-ordered l (only while building; mode 0 keeps it)
   DevBuf val;        // mode-ordered values
+  DevBuf val16;      // BF16 copy of val (made by the first BF16_REFINE sweep)
   DevBuf leaf;       // uint16
   DevBuf fib_start;  // uint32 K + 1
   DevBuf fib_mid;    // uint32 K
@@ -177,6 +178,7 @@ size_t dtype_size(mach_dtype dt) { return dt == MACH_F32 ? 4 : 8; }
 void free_mode(ModeCsf& m, cudaStream_t s, bool keep_idx) {
   if (!keep_idx) dev_free(m.idx, s);
   dev_free(m.val, s);
+  dev_free(m.val16, s);
   dev_free(m.leaf, s);
   dev_free(m.fib_start, s);
   dev_free(m.fib_mid, s);
@@ -609,14 +611,15 @@ mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
 }
 
 template <typename T>
-mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cudaStream_t st) {
+mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cudaStream_t st, bool bf16 = false) {
   const int d = h->d;
   const Cyc c = cyc(d, n);
   const ModeCsf& M = h->mode[n];
   TtmcLaunch L;
   L.d = d;
-  L.val = M.val.ptr;
+  L.val = bf16 ? M.val16.ptr : M.val.ptr;
   L.vdt = h->dt;
+  L.bf16 = bf16;
   L.leaf = static_cast<const uint16_t*>(M.leaf.ptr);
   L.fib_start = static_cast<const uint32_t*>(M.fib_start.ptr);
   L.fib_mid = static_cast<const uint32_t*>(M.fib_mid.ptr);
@@ -645,7 +648,8 @@ mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cu
   prof_begin(PROF_TTMC, st);
   MACH_TRY(launch_ttmc(L, sizeof(T) == 8, st));
   prof_end(PROF_TTMC, st,
-           (double)h->K * (dtype_size(h->dt) + 2) + (double)h->nfib[n] * 8 + (double)h->dims[n] * J * sizeof(T));
+           (double)h->K * ((bf16 ? 2 : dtype_size(h->dt)) + 2) + (double)h->nfib[n] * 8 +
+               (double)h->dims[n] * J * sizeof(T));
   return MACH_OK;
 }
 
@@ -689,9 +693,11 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
                               static_cast<T*>(w.fac[n].ptr), st);
 }
 
+constexpr int kBf16Refine = 3;   // FP32 refinement sweeps after the BF16 sweeps
+
 template <typename T>
 mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* const* factors, double* core,
-                      bool warm, cudaStream_t st) {
+                      bool warm, cudaStream_t st, bool bf16 = false) {
   const int d = h->d;
   Workspace& w = h->ws[sizeof(T) == 8 ? 1 : 0];
   MACH_TRY(ensure_ws<T>(h, ranks, w));
@@ -724,13 +730,28 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
       prof_end(PROF_INITGRAM, st, 0.0);
     }
   }
-  for (int sweep = 0; sweep < sweeps; ++sweep) {
+  if (bf16 && sweeps > 0) {
+    for (int n = 0; n < d; ++n) {
+      ModeCsf& M = h->mode[n];
+      if (!M.val16.ptr) {
+        MACH_TRY(dev_alloc(M.val16, (size_t)std::max<int64_t>(h->K, 1) * 2, st));
+        MACH_TRY(launch_to_bf16(M.val.ptr, h->dt, h->K, M.val16.ptr, st));
+      }
+    }
+  }
+  // BF16_REFINE: the requested sweeps read BF16 values, then kBf16Refine
+  // more sweeps with the input values refine every factor (subspace
+  // iteration from the BF16 solution; each sweep contracts the BF16 error
+  // by the HOOI convergence factor)
+  const int total = bf16 && sweeps > 0 ? sweeps + kBf16Refine : sweeps;
+  for (int sweep = 0; sweep < total; ++sweep) {
+    const bool low = bf16 && sweep < sweeps;
     for (int n = 0; n < d; ++n) {
       int J = 1;
       for (int k = 0; k < d; ++k)
         if (k != n) J *= ranks[k];
       const int In = (int)h->dims[n];
-      MACH_TRY(run_ttmc<T>(h, w, ranks, n, st));
+      MACH_TRY(run_ttmc<T>(h, w, ranks, n, st, low));
       prof_begin(PROF_LSV, st);
       const bool jroute = J < In;
       const int M = jroute ? J : In;
@@ -775,8 +796,9 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
   s->stream = st;
   switch (prec) {
     case MACH_PREC_FP64: return hooi_impl<double>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st);
-    case MACH_PREC_FP32:
-    case MACH_PREC_BF16_REFINE: return hooi_impl<float>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st);
+    case MACH_PREC_FP32: return hooi_impl<float>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st);
+    case MACH_PREC_BF16_REFINE:
+      return hooi_impl<float>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st, true);
   }
   return MACH_EINVAL;
 }

@@ -302,6 +302,7 @@ struct TtmcLaunch {
   int d;
   const void* val;
   mach_dtype vdt;
+  bool bf16 = false;          // val holds BF16 copies of the values
   const uint16_t* leaf;
   const uint32_t* fib_start;
   const uint32_t* fib_mid;
@@ -322,6 +323,8 @@ struct TtmcLaunch {
   unsigned* err;
 };
 uint32_t ttmc_task_max();
+// BF16 copy (round to nearest even) of K values of dtype dt.
+mach_status launch_to_bf16(const void* val, mach_dtype dt, int64_t K, void* out, cudaStream_t st);
 mach_status launch_ttmc(const TtmcLaunch& L, bool compute_fp64, cudaStream_t st);
 template <typename T>
 mach_status launch_gram(const T* Z, int64_t L, int M, int64_t sl, int64_t sm, T* C, T* partial_scratch,

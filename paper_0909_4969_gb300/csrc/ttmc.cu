@@ -23,6 +23,8 @@
 // so results are deterministic.
 #include "mach_internal.cuh"
 
+#include <cuda_bf16.h>
+
 namespace mach {
 
 namespace {
@@ -404,7 +406,31 @@ static mach_status launch_ttmc_vt(const TtmcLaunch& L, cudaStream_t st) {
   return MACH_EINVAL;
 }
 
+namespace {
+template <typename V>
+__global__ void to_bf16_kernel(const V* __restrict__ in, int64_t n, __nv_bfloat16* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn((float)in[i]);
+}
+}  // namespace
+
+mach_status launch_to_bf16(const void* val, mach_dtype dt, int64_t K, void* out, cudaStream_t st) {
+  if (K <= 0) return MACH_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(K, 256), (int64_t)num_sms() * 16);
+  if (dt == MACH_F32)
+    to_bf16_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(val), K, static_cast<__nv_bfloat16*>(out));
+  else
+    to_bf16_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(val), K,
+                                                 static_cast<__nv_bfloat16*>(out));
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
 mach_status launch_ttmc(const TtmcLaunch& L, bool compute_fp64, cudaStream_t st) {
+  if (L.bf16) {
+    if (compute_fp64) return MACH_EINVAL;
+    return launch_ttmc_vt<__nv_bfloat16, float>(L, st);
+  }
   if (L.vdt == MACH_F32) {
     return compute_fp64 ? launch_ttmc_vt<float, double>(L, st) : launch_ttmc_vt<float, float>(L, st);
   }

@@ -88,6 +88,29 @@ def test_uneven_ranks_and_matrix(prec):
     compare_decomposition(O, M, G_o, A_o, G_g, A_g, TOL[prec], prec + " matrix")
 
 
+@pytest.mark.parametrize("dims,ranks,core,p,sweeps", [
+    ((30, 28, 26, 24), (4, 4, 4, 4), "lognormal_sign", 0.2, 8),
+    ((120, 120, 120), (10, 10, 10), "gaussian", 0.05, 10),
+])
+def test_bf16_refine_matches_oracle(dims, ranks, core, p, sweeps):
+    """BF16_REFINE: `sweeps` sweeps read BF16 copies of the sampled values,
+    three more sweeps with the FP32 values refine every factor; against the
+    FP64 oracle run for the same total number of sweeps, within 1e-5."""
+    spec = synth.TuckerSpec(dims, ranks, core, 0.05, 2, "float32")
+    X, _, _ = synth.tucker_numpy(spec)
+    mach = mach_module()
+    S, G_o, A_o = O.mach_hooi(X.astype(np.float64), ranks, p, 21, sweeps + 3)
+    xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    s = mach.sample(xd, p, 21)
+    G, A = s.hooi(ranks, sweeps, "bf16_refine")
+    torch.cuda.synchronize()
+    st = s.stats()
+    assert st["flags"] == 0, st
+    s.free()
+    compare_decomposition(O, X.astype(np.float64), G_o, A_o, G.cpu().numpy(), [a.cpu().numpy() for a in A],
+                          TOL["fp32"], "bf16_refine %s" % (dims,))
+
+
 def test_exact_recovery_p_one():
     """Noise-free exact multilinear rank, p = 1: HOSVD is exact (Section 2.1)."""
     mach = mach_module()
