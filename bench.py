@@ -27,6 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "bf16_refine": "bf16+f32"}
 METRIC = "Tucker decomps/sec + sampler HBM GB/s vs plain FP64 form at ≤1e-5 err; p50/p99"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -37,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mach", choices=["mach", "reference"])
-    ap.add_argument("--workload", default="large_fp32", choices=["large_fp32", "plain_fp64", "served", "batched"])
+    ap.add_argument("--workload", default="large_fp32", choices=["large_fp32", "plain_fp64", "mixed_4way", "served", "batched"])
     ap.add_argument("--requests", type=int, default=400, help="served: requests in the timed run")
     ap.add_argument("--slots", type=int, default=8, help="served / batched: concurrent slots")
     ap.add_argument("--budget-gb", type=float, default=48.0, help="served / batched: HBM budget")
@@ -55,6 +56,8 @@ def workload(args):
     from paper_0909_4969_gb300 import synth
     if args.workload == "plain_fp64":
         w = synth.config_plain_fp64()
+    elif args.workload == "mixed_4way":
+        w = synth.config_mixed_4way(200 if args.scale == 1000 else args.scale)
     else:
         w = synth.config_large_fp32(args.scale)
     prec = args.prec or w.precision
@@ -271,7 +274,7 @@ def run_served(args):
     clk = clocks.stop()
     line = {"metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": 1, "steps": args.requests,
             "warmup": max(32, 16 * args.warmup), "ms_per_step": 1e3 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME.get(prec, prec),
             "data": "synthetic",
             "config": {"workload": "served_stream_64x200x16x512", "streams": n_streams, "window": list(small),
                        "resized_window": list(big), "resize_frac": 0.10, "rate_hz": 2000.0, "p": p,
@@ -321,7 +324,7 @@ def run_batched(args):
     plain, st64, errs64 = run("fp64", 1, items)
     line = {"metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": 1, "steps": len(items),
             "warmup": 32, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE_NAME.get(prec, prec), "data": "synthetic",
             "config": {"workload": "batched_%d_uneven" % len(items), "ranks": list(ranks), "p": 0.1, "sweeps": 10,
                        "noise": 0.10, "slots": args.slots, "budget_gb": args.budget_gb, "prec": prec,
                        "total_input_gb": sum(x.numel() * 4 for x in xs) / 1e9},
@@ -496,7 +499,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME.get(prec, prec),
                 "data": "synthetic", "config": config_dict(w, prec),
                 "p50_ms": statistics.median(per_step),
                 "p99_ms": sorted(per_step)[max(0, math.ceil(0.99 * len(per_step)) - 1)],

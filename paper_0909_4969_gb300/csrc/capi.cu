@@ -722,10 +722,10 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
                                               static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
                                               h->K, In, static_cast<T*>(w.C.ptr), st)));
       // With sweeps to follow, HOOI refines the start, so the HOSVD Gram's
-      // eigenvectors are iterated at most 40 times (FP64) or 12 times (FP32,
+      // eigenvectors are iterated at most 40 times (FP64) or 8 times (FP32,
       // whose results are compared at 1e-5); MACH-HOSVD alone (no sweeps)
       // iterates to convergence (at most 400).
-      const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 12) : 400;
+      const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 8) : 400;
       MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, init_it, factors[n], st));
       prof_end(PROF_INITGRAM, st, 0.0);
     }

@@ -180,6 +180,7 @@ __global__ void copy_cols(const T* __restrict__ A, int M, int r, T* V, int b) {
 // (deterministic), factors G = R^T R and stores R^-1 (upper) in rinv.
 // ----------------------------------------------------------------------------
 constexpr int kPairsPerLane = (kMaxRank * kMaxRank + 31) / 32;
+constexpr size_t kLsvStageBytes = 48 * 1024;
 
 template <typename T>
 __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y, const double* __restrict__ Vout,
@@ -189,6 +190,13 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
   __shared__ double wsum[8][kMaxRank * kMaxRank];
   __shared__ double sinv[kMaxRank];
   __shared__ bool last;
+  // the row products Y V run in the arithmetic of Y (T); V is staged in
+  // shared memory in T when it fits
+  extern __shared__ __align__(16) unsigned char lsv_smem[];
+  T* Vs = reinterpret_cast<T*>(lsv_smem);
+  const bool staged = jroute && (size_t)J * r * sizeof(T) <= kLsvStageBytes;
+  if (staged)
+    for (int e = threadIdx.x; e < J * r; e += blockDim.x) Vs[e] = (T)Vout[e];
   if (threadIdx.x < r) sinv[threadIdx.x] = theta[threadIdx.x] > 0.0 ? 1.0 / sqrt(theta[threadIdx.x]) : 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -199,17 +207,23 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
   for (int i = blockIdx.x * nw + warp; i < I; i += gridDim.x * nw) {
     double arow[kMaxRank];
     if (jroute) {
-      double sacc[kMaxRank];
+      T sacc[kMaxRank];
 #pragma unroll
-      for (int k = 0; k < kMaxRank; ++k) sacc[k] = 0.0;
+      for (int k = 0; k < kMaxRank; ++k) sacc[k] = T(0);
       for (int j = lane; j < J; j += 32) {
-        const double y = (double)Y[(size_t)i * J + j];
+        const T y = Y[(size_t)i * J + j];
+        if (staged) {
 #pragma unroll
-        for (int k = 0; k < kMaxRank; ++k)
-          if (k < r) sacc[k] += y * Vout[(size_t)j * r + k];
+          for (int k = 0; k < kMaxRank; ++k)
+            if (k < r) sacc[k] += y * Vs[j * r + k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < kMaxRank; ++k)
+            if (k < r) sacc[k] += y * (T)Vout[(size_t)j * r + k];
+        }
       }
 #pragma unroll
-      for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? warp_sum(sacc[k]) * sinv[k] : 0.0;
+      for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? (double)warp_sum(sacc[k]) * sinv[k] : 0.0;
     } else {
 #pragma unroll
       for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? Vout[(size_t)i * r + k] : 0.0;
@@ -392,8 +406,10 @@ mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* thet
                               double* out_colmajor, T* out_rowmajor, cudaStream_t st) {
   MACH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 8), 2 * num_sms()));
-  lsv_apply_kernel<T><<<blocks, 256, 0, st>>>(Y, Vout, theta, I, J, r, jroute ? 1 : 0, A64, gram64, counter, rinv,
-                                               err);
+  const size_t vbytes = (size_t)J * r * sizeof(T);
+  const size_t smem = jroute && vbytes <= kLsvStageBytes ? vbytes : 0;
+  lsv_apply_kernel<T><<<blocks, 256, smem, st>>>(Y, Vout, theta, I, J, r, jroute ? 1 : 0, A64, gram64, counter,
+                                                  rinv, err);
   MACH_LAUNCH_CHECK();
   lsv_finish_kernel<T><<<(unsigned)ceil_div((int64_t)I * r, 256), 256, 0, st>>>(A64, rinv, I, r, out_colmajor,
                                                                                  out_rowmajor);
