@@ -255,14 +255,14 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // deterministic sum of the partials: entry e on warp e mod nw, lane l sums
-  // blocks l, l + 32, .. in order, then a fixed butterfly across the lanes
+  // deterministic sum of the partials in block order, one thread per entry
+  // (the loads are independent, so they are all in flight at once)
   double* G = &wsum[0][0];
-  for (int e = warp; e < rr; e += nw) {
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
     double t = 0.0;
-    for (unsigned k = lane; k < gridDim.x; k += 32) t += __ldcg(part + (size_t)k * rr + e);
-    t = warp_sum(t);
-    if (lane == 0) G[e] = t;
+#pragma unroll 8
+    for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(part + (size_t)k * rr + e);
+    G[e] = t;
   }
   __syncthreads();
   if (warp != 0) return;
@@ -405,7 +405,8 @@ mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* thet
                               double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
                               double* out_colmajor, T* out_rowmajor, cudaStream_t st) {
   MACH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 8), 2 * num_sms()));
+  // few partial Grams for the last CTA to sum: at most 64 CTAs, several rows per warp
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 32), 64));
   const size_t vbytes = (size_t)J * r * sizeof(T);
   const size_t smem = jroute && vbytes <= kLsvStageBytes ? vbytes : 0;
   lsv_apply_kernel<T><<<blocks, 256, smem, st>>>(Y, Vout, theta, I, J, r, jroute ? 1 : 0, A64, gram64, counter,
