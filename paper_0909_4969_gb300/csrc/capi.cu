@@ -351,38 +351,57 @@ mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_
   if ((s = dev_alloc(h->scal, sizeof(SampleScalars), st)) != MACH_OK) return fail(s);
   SampleScalars* ds = h->dscal();
   if (cudaMemsetAsync(ds, 0, sizeof(SampleScalars), st) != cudaSuccess) return fail(MACH_ECUDA);
-  const double q = (double)h->T / 4294967296.0;
-  const double mean = (double)N * q;
-  int64_t cap = (int64_t)(mean + 10.0 * std::sqrt(mean * (1.0 - q) + 1.0) + 4096.0);
-  if (cap > N || h->T >= (1ull << 32)) cap = N;
-  DevBuf scratch;
+  // coin + compaction: per-CTA segments, then an ordered gather into idx / val
+  // (sized for the segments' capacity, so no host round trip in between)
+  const double q = h->T >= (1ull << 32) ? 1.0 : (double)h->T / 4294967296.0;
+  SegPlan pl = plan_segments(N, dtype, q);
   const size_t vs = dtype_size(dtype);
   for (int attempt = 0; attempt < 2; ++attempt) {
-    if ((s = dev_alloc(h->idx, (size_t)cap * 8, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(h->val, (size_t)cap * vs, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(scratch, (size_t)sampler_scratch_words(N, dtype) * 8, st)) != MACH_OK) return fail(s);
+    DevBuf seg_idx, seg_val, seg_cnt;
+    const int64_t cap_all = pl.nseg * pl.seg_cap;
+    if ((s = dev_alloc(h->idx, (size_t)cap_all * 8, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(h->val, (size_t)cap_all * vs, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(seg_idx, (size_t)cap_all * 8, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(seg_val, (size_t)cap_all * vs, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(seg_cnt, (size_t)pl.nseg * 8, st)) != MACH_OK) return fail(s);
     prof_begin(PROF_SAMPLER, st);
-    if ((s = launch_sampler(x_dev, dtype, N, seed, h->T, cap, static_cast<int64_t*>(h->idx.ptr), h->val.ptr,
-                            &ds->count, &ds->err, static_cast<unsigned long long*>(scratch.ptr), st)) != MACH_OK)
+    if ((s = launch_sampler_seg(x_dev, dtype, N, seed, h->T, pl, static_cast<int64_t*>(seg_idx.ptr), seg_val.ptr,
+                                static_cast<int64_t*>(seg_cnt.ptr), &ds->err, st)) != MACH_OK)
+      return fail(s);
+    if ((s = launch_seg_gather(dtype, pl, static_cast<const int64_t*>(seg_cnt.ptr),
+                               static_cast<const int64_t*>(seg_idx.ptr), seg_val.ptr,
+                               static_cast<int64_t*>(h->idx.ptr), h->val.ptr, cap_all, &ds->err, st)) != MACH_OK)
       return fail(s);
     prof_end(PROF_SAMPLER, st, 0.0);
-    dev_free(scratch, st);
+    std::vector<int64_t> cnt((size_t)pl.nseg);
     SampleScalars hs;
-    if (cudaMemcpyAsync(&hs, ds, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(cnt.data(), seg_cnt.ptr, cnt.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&hs, ds, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       set_last_error("sampler: %s", cudaGetErrorString(cudaGetLastError()));
       return fail(MACH_ECUDA);
     }
+    dev_free(seg_idx, st);
+    dev_free(seg_val, st);
+    dev_free(seg_cnt, st);
     if (hs.err & DEV_TIMEOUT) return fail(MACH_ETIMEOUT);
-    h->K = hs.count;
-    prof_patch_last_bytes(PROF_SAMPLER, (double)N * vs + (double)hs.count * (vs + 8));
-    if (!(hs.err & DEV_OVERFLOW)) break;
-    // capacity exceeded (a > 10-sigma event): retry with the exact count
+    int64_t K = 0, mx = 0;
+    for (int64_t c : cnt) {
+      K += c;
+      mx = std::max(mx, c);
+    }
+    h->K = K;
+    prof_patch_last_bytes(PROF_SAMPLER, (double)N * vs + (double)K * (vs + 8));
+    if (!(hs.err & DEV_OVERFLOW) && mx <= pl.seg_cap) break;
+    // a segment exceeded its capacity (an 8-sigma event): rerun with the exact one
     dev_free(h->idx, st);
     dev_free(h->val, st);
     cudaMemsetAsync(&ds->err, 0, sizeof(unsigned), st);
-    cap = std::max<int64_t>(hs.count, 1);
+    pl.seg_cap = std::max<int64_t>(mx, 1);
   }
+  if (cudaMemcpyAsync(&ds->count, &h->K, sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(MACH_ECUDA);
   const int64_t K = h->K;
   if (K >= (1ll << 31)) {
     set_last_error("too many kept entries (%lld) for 32-bit fibre indices", (long long)K);

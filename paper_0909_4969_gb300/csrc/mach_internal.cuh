@@ -266,6 +266,20 @@ int num_sms();
 // linalg.cu / error.cu) and their argument blocks.
 // ----------------------------------------------------------------------------
 int64_t sampler_scratch_words(int64_t n, mach_dtype dt);
+// Segmented sampler (sample.cu): nseg CTAs, each writing up to seg_cap kept
+// pairs of its contiguous tiles into its own segment; then an ordered gather.
+struct SegPlan {
+  int64_t nseg = 0;
+  int64_t tiles_per_cta = 0;
+  int64_t seg_cap = 0;
+};
+SegPlan plan_segments(int64_t n, mach_dtype dt, double q);
+mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
+                               int64_t* seg_idx, void* seg_val, int64_t* seg_count, unsigned* d_err,
+                               cudaStream_t st);
+mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const int64_t* seg_idx,
+                              const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
+                              cudaStream_t st);
 // Fixed scratch of the allocation-free sampler (sample.cu): its size in
 // 8-byte words, the largest tensor it serves, and this device's address of it.
 constexpr int64_t kFixedScratchWords = 524288;

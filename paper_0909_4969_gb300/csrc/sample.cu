@@ -17,6 +17,7 @@
 // Philox is evaluated exactly once per counter; every wait is bounded.
 #include "mach_internal.cuh"
 
+#include <cmath>
 #include <mutex>
 
 namespace mach {
@@ -343,7 +344,239 @@ mach_status launch_sampler_t(const void* x, int64_t n, uint64_t seed, uint64_t T
   return MACH_OK;
 }
 
+// ----------------------------------------------------------------------------
+// Segmented sampler (the product path of mach_sample).  Each CTA owns a
+// contiguous range of tiles and writes its kept (l, value) pairs, in
+// increasing l, into its own segment of a staging buffer; seg_gather_kernel
+// then concatenates the segments in CTA order, which is increasing l
+// overall.  No CTA ever waits for another.  Per tile the coin is evaluated
+// before the tile's bytes are waited for (it depends on l only), so the
+// Philox arithmetic overlaps the TMA stream of the 3-stage ring; 4 CTAs of
+// 8 warps per SM keep the integer pipes busy.
+// ----------------------------------------------------------------------------
+constexpr int kSegThreads = 256;
+constexpr int kSegStages = 3;
+
+struct SegArgs {
+  const void* x;
+  int64_t n;
+  uint32_t key0, key1;
+  uint32_t t32;
+  int keep_all;
+  int64_t num_tiles;
+  int64_t tiles_per_cta;
+  int64_t seg_cap;
+  int64_t* seg_idx;
+  void* seg_val;
+  int64_t* seg_count;
+  unsigned* err;
+};
+
+template <typename V>
+__global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
+  using C = SampCfg<V>;
+  static_assert(C::kTile == kSegThreads * C::kEPT, "tile layout");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  V* stage = reinterpret_cast<V*>(smem_raw);
+  __shared__ uint64_t bar[kSegStages];
+  __shared__ int warp_tot[kSegThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const V* x = static_cast<const V*>(a.x);
+  const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_cta;
+  const int64_t t1 = min(a.num_tiles, t0 + a.tiles_per_cta);
+  if (tid == 0) {
+    for (int s = 0; s < kSegStages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // thread 0: bulk copy of tile t into stage s (16-byte-floored length; a
+  // ragged tail is read directly)
+  auto issue = [&](int64_t t, int s) {
+    const int64_t e0 = t * C::kTile;
+    const int64_t ne = min((int64_t)C::kTile, a.n - e0);
+    const uint32_t bytes = (uint32_t)(((uint64_t)ne * sizeof(V)) & ~(uint64_t)15);
+    fence_proxy_async_smem();
+    if (bytes) {
+      mbar_arrive_expect_tx(&bar[s], bytes);
+      bulk_g2s(stage + (size_t)s * C::kTile, x + e0, bytes, &bar[s]);
+    } else {
+      mbar_arrive(&bar[s]);
+    }
+  };
+  if (tid == 0)
+    for (int s = 0; s < kSegStages && t0 + s < t1; ++s) issue(t0 + s, s);
+  int64_t* out_idx = a.seg_idx + (size_t)blockIdx.x * a.seg_cap;
+  V* out_val = static_cast<V*>(a.seg_val) + (size_t)blockIdx.x * a.seg_cap;
+  int64_t base = 0;
+  int j = 0;
+  for (int64_t t = t0; t < t1; ++t, ++j) {
+    const int s = j % kSegStages;
+    // the coin of this thread's entries (no data needed)
+    const int64_t e_thr = t * C::kTile + (int64_t)tid * C::kEPT;
+    const uint64_t q0 = (uint64_t)e_thr >> 2;
+    uint32_t mask = 0;
+#pragma unroll
+    for (int c = 0; c < C::kCPT; ++c) {
+      const uint64_t q = q0 + c;
+      const uint4 w = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), a.key0, a.key1);
+      uint32_t b;
+      if (a.keep_all) {
+        b = 0xFu;
+      } else {
+        b = (uint32_t)(w.x < a.t32) | ((uint32_t)(w.y < a.t32) << 1) | ((uint32_t)(w.z < a.t32) << 2) |
+            ((uint32_t)(w.w < a.t32) << 3);
+      }
+      mask |= b << (4 * c);
+    }
+    const int64_t valid = a.n - e_thr;
+    if (valid < C::kEPT) mask &= valid <= 0 ? 0u : ((1u << valid) - 1u);
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(j / kSegStages) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(a.err, DEV_TIMEOUT);
+        for (int q = 1; q < kSegStages; ++q)
+          if (t + q < t1) (void)mbar_wait_bounded(&bar[(j + q) % kSegStages], (uint32_t)((j + q) / kSegStages) & 1u);
+      }
+      return;
+    }
+    int warp_off = 0, blk = 0;
+#pragma unroll
+    for (int w = 0; w < kSegThreads / 32; ++w) {
+      const int v = warp_tot[w];
+      warp_off += (w < warp) ? v : 0;
+      blk += v;
+    }
+    if (mask) {
+      const V* buf = stage + (size_t)s * C::kTile;
+      const int64_t e_tile = t * C::kTile;
+      const int64_t tile_n = min((int64_t)C::kTile, a.n - e_tile);
+      const int64_t n_staged = (int64_t)((((uint64_t)tile_n * sizeof(V)) & ~(uint64_t)15) / sizeof(V));
+      int64_t pos = base + warp_off + incl - cnt;
+      while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int64_t l = e_thr + b;
+        const int64_t in_tile = l - e_tile;
+        const V v = in_tile < n_staged ? buf[in_tile] : x[l];
+        if (pos < a.seg_cap) {
+          out_idx[pos] = l;
+          out_val[pos] = v;
+        }
+        ++pos;
+      }
+    }
+    base += blk;
+    __syncthreads();   // stage s and warp_tot are free again
+    if (tid == 0 && t + kSegStages < t1) issue(t + kSegStages, s);
+  }
+  if (tid == 0) a.seg_count[blockIdx.x] = base;
+}
+
+// Concatenate the segments in CTA order into idx / val[0, K); block c
+// copies segment c.  Segments that overflowed their capacity are flagged
+// (the host then reruns with the exact capacity).
+template <typename V>
+__global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restrict__ seg_count, int64_t seg_cap,
+                                                         const int64_t* __restrict__ seg_idx,
+                                                         const V* __restrict__ seg_val, int64_t* __restrict__ idx,
+                                                         V* __restrict__ val, int64_t out_cap, unsigned* err) {
+  __shared__ int64_t off;
+  const int c = blockIdx.x;
+  if (threadIdx.x < 32) {
+    int64_t s = 0;
+    for (int k = threadIdx.x; k < c; k += 32) s += seg_count[k];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) off = s;
+  }
+  __syncthreads();
+  const int64_t cnt = seg_count[c];
+  if (cnt > seg_cap) {
+    if (threadIdx.x == 0) atomicOr(err, DEV_OVERFLOW);
+    return;
+  }
+  if (off + cnt > out_cap) {
+    if (threadIdx.x == 0) atomicOr(err, DEV_OVERFLOW);
+    return;
+  }
+  const int64_t* si = seg_idx + (size_t)c * seg_cap;
+  const V* sv = seg_val + (size_t)c * seg_cap;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    idx[off + i] = si[i];
+    val[off + i] = sv[i];
+  }
+}
+
+template <typename V>
+mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl, int64_t* seg_idx,
+                         void* seg_val, int64_t* seg_count, unsigned* d_err, cudaStream_t st) {
+  using C = SampCfg<V>;
+  SegArgs a;
+  a.x = x;
+  a.n = n;
+  a.key0 = (uint32_t)(seed & 0xffffffffu);
+  a.key1 = (uint32_t)(seed >> 32);
+  a.keep_all = T >= (1ull << 32) ? 1 : 0;
+  a.t32 = a.keep_all ? 0xffffffffu : (uint32_t)T;
+  a.num_tiles = ceil_div(n, C::kTile);
+  a.tiles_per_cta = pl.tiles_per_cta;
+  a.seg_cap = pl.seg_cap;
+  a.seg_idx = seg_idx;
+  a.seg_val = seg_val;
+  a.seg_count = seg_count;
+  a.err = d_err;
+  const size_t smem = kSegStages * C::kStageBytes;
+  MACH_TRY(allow_max_dyn_smem(sample_seg_kernel<V>));
+  sample_seg_kernel<V><<<(unsigned)pl.nseg, kSegThreads, smem, st>>>(a);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
 }  // namespace
+
+SegPlan plan_segments(int64_t n, mach_dtype dt, double q) {
+  const int64_t tile = dt == MACH_F32 ? SampCfg<float>::kTile : SampCfg<double>::kTile;
+  const int64_t num_tiles = std::max<int64_t>(1, ceil_div(n, tile));
+  int64_t nseg = std::min<int64_t>(num_tiles, (int64_t)num_sms() * 4);
+  SegPlan pl;
+  pl.tiles_per_cta = ceil_div(num_tiles, nseg);
+  pl.nseg = ceil_div(num_tiles, pl.tiles_per_cta);
+  const double per = (double)pl.tiles_per_cta * (double)tile;
+  const double mean = per * q;
+  int64_t cap = (int64_t)(mean + 8.0 * std::sqrt(mean * (1.0 - q) + 1.0) + 256.0);
+  if (cap > (int64_t)per || q >= 1.0) cap = (int64_t)per;
+  pl.seg_cap = std::max<int64_t>(cap, 1);
+  return pl;
+}
+
+mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
+                               int64_t* seg_idx, void* seg_val, int64_t* seg_count, unsigned* d_err,
+                               cudaStream_t st) {
+  if (dt == MACH_F32) return launch_seg_t<float>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
+  return launch_seg_t<double>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
+}
+
+mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const int64_t* seg_idx,
+                              const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
+                              cudaStream_t st) {
+  if (dt == MACH_F32)
+    seg_gather_kernel<float><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, seg_idx,
+                                                                 static_cast<const float*>(seg_val), idx,
+                                                                 static_cast<float*>(val), out_cap, d_err);
+  else
+    seg_gather_kernel<double><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, seg_idx,
+                                                                  static_cast<const double*>(seg_val), idx,
+                                                                  static_cast<double*>(val), out_cap, d_err);
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
 
 int64_t sampler_scratch_words(int64_t n, mach_dtype dt) {
   const int64_t tile = dt == MACH_F32 ? SampCfg<float>::kTile : SampCfg<double>::kTile;
