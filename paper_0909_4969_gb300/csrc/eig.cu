@@ -222,6 +222,25 @@ __device__ void col_scale_warp(const T* G, int n, T* d) {
   __syncwarp();
 }
 
+// row[0..b) <- row D R^-1 for the upper factor R (shared memory, ld kLd)
+// of a rank-revealing Cholesky (dead columns zeroed).  Unrolled over the
+// kB columns so that the row stays in registers.
+template <typename T>
+__device__ __forceinline__ void solve_row(T (&row)[kB], const T* d, const T* R, const int* dead, int b) {
+#pragma unroll
+  for (int j = 0; j < kB; ++j)
+    if (j < b) row[j] *= d[j];
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    if (j < b) {
+      T v = row[j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= row[k] * R[k * kLd + j];
+      row[j] = dead[j] ? T(0) : v / R[j * kLd + j];
+    }
+  }
+}
+
 // Shared state of one b-space step.
 template <typename T>
 struct BSpace {
@@ -316,13 +335,12 @@ __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev
   // S <- S D R^-1: forward substitution against upper R, one row per thread
   if (tid < b) {
     T row[kB];
-    for (int j = 0; j < b; ++j) row[j] = s.S[tid * kLd + j] * s.d[j];
-    for (int j = 0; j < b; ++j) {
-      T v = row[j];
-      for (int k = 0; k < j; ++k) v -= row[k] * s.F[k * kLd + j];
-      row[j] = s.dead[j] ? T(0) : v / s.F[j * kLd + j];
-    }
-    for (int j = 0; j < b; ++j) s.S[tid * kLd + j] = row[j];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) row[j] = j < b ? s.S[tid * kLd + j] : T(0);
+    solve_row<T>(row, s.d, s.F, s.dead, b);
+#pragma unroll
+    for (int j = 0; j < kB; ++j)
+      if (j < b) s.S[tid * kLd + j] = row[j];
   }
   __syncthreads();
 }
@@ -676,18 +694,15 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     V = reinterpret_cast<T*>(eig_smem);
     W = V + (size_t)M * ld;
     U = W + (size_t)M * ld;
-    for (int o = threadIdx.x; o < M * b; o += blockDim.x) {
-      const int i = o / b, j = o - (o / b) * b;
-      V[i * ld + j] = a.V[o];
-    }
+    // rows on warps, columns on lanes (coalesced, no division)
+    for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+      for (int j = threadIdx.x & 31; j < b; j += 32) V[i * ld + j] = a.V[(size_t)i * b + j];
   }
   if (smem_mode == 2) {
     T* Cs = U + (size_t)M * ld;
     ldc = M | 1;
-    for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
-      const int i = o / M, k = o - (o / M) * M;
-      Cs[i * ldc + k] = a.C[o];
-    }
+    for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+      for (int k = threadIdx.x & 31; k < M; k += 32) Cs[i * ldc + k] = a.C[(size_t)i * M + k];
     C = Cs;
   }
   if (threadIdx.x == 0) prev = 1e300;
@@ -705,13 +720,12 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     // S = D R^-1 (upper): solve row by row of the identity scaled by D
     if (lane < b) {
       T row[kB];
-      for (int j = 0; j < b; ++j) row[j] = (j == lane) ? bs.d[lane] : T(0);
-      for (int j = 0; j < b; ++j) {
-        T v = row[j];
-        for (int k = 0; k < j; ++k) v -= row[k] * bs.G[k * kLd + j];
-        row[j] = bs.dead[j] ? T(0) : v / bs.G[j * kLd + j];
-      }
-      for (int j = 0; j < b; ++j) bs.S[lane * kLd + j] = row[j];
+#pragma unroll
+      for (int j = 0; j < kB; ++j) row[j] = j == lane ? T(1) : T(0);
+      solve_row<T>(row, bs.d, bs.G, bs.dead, b);
+#pragma unroll
+      for (int j = 0; j < kB; ++j)
+        if (j < b) bs.S[lane * kLd + j] = row[j];
     }
   }
   __syncthreads();
@@ -898,13 +912,12 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
       chol_warp<T>(bs.G, b, bs.dead);
       if (lane < b) {
         T row[kB];
-        for (int j = 0; j < b; ++j) row[j] = (j == lane) ? bs.d[lane] : T(0);
-        for (int j = 0; j < b; ++j) {
-          T v = row[j];
-          for (int k = 0; k < j; ++k) v -= row[k] * bs.G[k * kLd + j];
-          row[j] = bs.dead[j] ? T(0) : v / bs.G[j * kLd + j];
-        }
-        for (int j = 0; j < b; ++j) bs.S[lane * kLd + j] = row[j];
+#pragma unroll
+        for (int j = 0; j < kB; ++j) row[j] = j == lane ? T(1) : T(0);
+        solve_row<T>(row, bs.d, bs.G, bs.dead, b);
+#pragma unroll
+        for (int j = 0; j < kB; ++j)
+          if (j < b) bs.S[lane * kLd + j] = row[j];
       }
     } else {
       // symmetrise H (rounding) before Jacobi
