@@ -149,36 +149,32 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
       bulk_g2s(wb + WarpStage<V>::kValBytes, a.leaf + b0, lb, &bar_warp[warp][buf]);
     }
   };
-  if ((uint32_t)gwarp < ntask) stage_task((uint32_t)gwarp, 0);
+  // each warp takes a contiguous block of tasks [tb, te) and keeps its
+  // accumulators across consecutive tasks of one row: one output per (warp,
+  // row) run, written straight to Y when the row lies inside the block, else
+  // to the partial slot of the run's first task (summed by the fix-up)
+  const uint32_t per = (ntask + (uint32_t)nwarps - 1u) / (uint32_t)nwarps;
+  const uint32_t tb = min(ntask, (uint32_t)gwarp * per), te = min(ntask, tb + per);
+  if (tb < te) stage_task(tb, 0);
   int cur = 0;
+  T acc[ACC];
+#pragma unroll
+  for (int s = 0; s < ACC; ++s) acc[s] = T(0);
+  // d = 3: lane (h, am) = (lane >> 4, lane & 15) folds the fibres j = h,
+  // h + 2, .. into row am of the (r_mid x r_leaf) block: acc3[b] +=
+  // A_mid[i_mid(f_j), am] z_j[b]  (z_j read as a broadcast)
+  T acc3[D == 3 ? RLM : 1];
+#pragma unroll
+  for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] = T(0);
+  const int half = lane >> 4, am = lane & 15;
+  T w[D == 4 ? kSQ : 1];
+#pragma unroll
+  for (int s = 0; s < (D == 4 ? kSQ : 1); ++s) w[s] = T(0);
+  uint32_t cur_a1 = 0xffffffffu;
+  int cur_row = -1;
+  uint32_t head = 0;
 
-  for (uint32_t t = gwarp; t < ntask; t += nwarps, cur ^= 1) {
-    // prefetch the next task into the other buffer (freed at the end of the
-    // previous iteration) while this one is processed
-    if (t + nwarps < ntask) stage_task(t + nwarps, cur ^ 1);
-    const int4 tk = a.tasks[t];
-    const int row = tk.x;
-    const uint32_t e0 = (uint32_t)tk.y, e1 = (uint32_t)tk.z;
-    const uint32_t base = e0 & ~(kAlign - 1);
-    unsigned char* wbuf = wbuf0 + (size_t)cur * WarpStage<V>::kBytes;
-    const V* sval = reinterpret_cast<const V*>(wbuf);
-    const uint16_t* sleaf = reinterpret_cast<const uint16_t*>(wbuf + WarpStage<V>::kValBytes);
-    T acc[ACC];
-#pragma unroll
-    for (int s = 0; s < ACC; ++s) acc[s] = T(0);
-    // d = 3: lane (h, am) = (lane >> 4, lane & 15) folds the fibres j = h,
-    // h + 2, .. into row am of the (r_mid x r_leaf) block: acc3[b] +=
-    // A_mid[i_mid(f_j), am] z_j[b]  (z_j read as a broadcast)
-    T acc3[D == 3 ? RLM : 1];
-#pragma unroll
-    for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] = T(0);
-    const int half = lane >> 4, am = lane & 15;
-    T w[D == 4 ? kSQ : 1];
-#pragma unroll
-    for (int s = 0; s < (D == 4 ? kSQ : 1); ++s) w[s] = T(0);
-    uint32_t cur_a1 = 0xffffffffu;
-
-    auto flush_w = [&]() {
+  auto flush_w = [&]() {
       if (D == 4 && cur_a1 != 0xffffffffu) {
         const T* arow = Amid0 + (size_t)cur_a1 * a.r_mid0;
 #pragma unroll
@@ -195,10 +191,64 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
       }
     };
 
+  auto flush_row = [&]() {
+    flush_w();
+    cur_a1 = 0xffffffffu;
+    const uint32_t rt0 = a.row_task[cur_row], rt1 = a.row_task[cur_row + 1];
+    const bool whole = rt0 >= tb && rt1 <= te;
+    T* dst = whole ? a.Y + (size_t)cur_row * a.J : a.partial + (size_t)head * a.J;
+    if (D == 4) {
+#pragma unroll
+      for (int r1 = 0; r1 < kMaxRank; ++r1) {
+        if (r1 < a.r_mid0) {
+#pragma unroll
+          for (int s = 0; s < kSQ; ++s) {
+            const int q = lane + 32 * s;
+            if (s < SQ && q < Q && r1 * SQ + s < ACC) dst[r1 * Q + q] = acc[r1 * SQ + s];
+          }
+        }
+      }
+    } else if (D == 3) {
+#pragma unroll
+      for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] += __shfl_xor_sync(0xffffffffu, acc3[b], 16);
+      if (half == 0 && am < a.r_mid0) {
+#pragma unroll
+        for (int b = 0; b < (D == 3 ? RLM : 1); ++b)
+          if (b < rl) dst[am * rl + b] = acc3[b];
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < ACC; ++s) {
+        const int q = lane + 32 * s;
+        if (q < a.J) dst[q] = acc[s];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < ACC; ++s) acc[s] = T(0);
+#pragma unroll
+    for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] = T(0);
+  };
+
+  for (uint32_t t = tb; t < te; ++t, cur ^= 1) {
+    // prefetch the next task into the other buffer (freed at the end of the
+    // previous iteration) while this one is processed
+    if (t + 1 < te) stage_task(t + 1, cur ^ 1);
+    const int4 tk = a.tasks[t];
+    const int row = tk.x;
+    const uint32_t e0 = (uint32_t)tk.y, e1 = (uint32_t)tk.z;
+    const uint32_t base = e0 & ~(kAlign - 1);
+    unsigned char* wbuf = wbuf0 + (size_t)cur * WarpStage<V>::kBytes;
+    const V* sval = reinterpret_cast<const V*>(wbuf);
+    const uint16_t* sleaf = reinterpret_cast<const uint16_t*>(wbuf + WarpStage<V>::kValBytes);
+    if (row != cur_row) {
+      if (cur_row >= 0) flush_row();
+      cur_row = row;
+      head = t;
+    }
     if (!mbar_wait_bounded(&bar_warp[warp][cur], (phase_bits >> cur) & 1u)) {
       if (lane == 0) atomicOr(a.err, DEV_TIMEOUT);
       // drain the prefetch of the other buffer (bounded) before leaving
-      if (t + nwarps < ntask) (void)mbar_wait_bounded(&bar_warp[warp][cur ^ 1], (phase_bits >> (cur ^ 1)) & 1u);
+      if (t + 1 < te) (void)mbar_wait_bounded(&bar_warp[warp][cur ^ 1], (phase_bits >> (cur ^ 1)) & 1u);
       return;
     }
     phase_bits ^= 1u << cur;
@@ -271,49 +321,28 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
       }
       __syncwarp();
     }
-    flush_w();
-
-    const bool single = (a.row_task[row + 1] - a.row_task[row]) == 1;
-    T* dst = single ? a.Y + (size_t)row * a.J : a.partial + (size_t)t * a.J;
-    if (D == 4) {
-#pragma unroll
-      for (int r1 = 0; r1 < kMaxRank; ++r1) {
-        if (r1 < a.r_mid0) {
-#pragma unroll
-          for (int s = 0; s < kSQ; ++s) {
-            const int q = lane + 32 * s;
-            if (s < SQ && q < Q && r1 * SQ + s < ACC) dst[r1 * Q + q] = acc[r1 * SQ + s];
-          }
-        }
-      }
-    } else if (D == 3) {
-#pragma unroll
-      for (int b = 0; b < (D == 3 ? RLM : 1); ++b) acc3[b] += __shfl_xor_sync(0xffffffffu, acc3[b], 16);
-      if (half == 0 && am < a.r_mid0) {
-#pragma unroll
-        for (int b = 0; b < (D == 3 ? RLM : 1); ++b)
-          if (b < rl) dst[am * rl + b] = acc3[b];
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < ACC; ++s) {
-        const int q = lane + 32 * s;
-        if (q < a.J) dst[q] = acc[s];
-      }
-    }
     __syncwarp();   // the staging buffer is reused by the next task
   }
+  if (cur_row >= 0) flush_row();
 }
 
+// Rows split over several warps' task blocks: Y_row = sum of the partials of
+// the runs, i.e. of the row's first task and of every later task that starts
+// a warp block (t a multiple of `per`), in increasing task order.  Rows that
+// lie in one block were written directly; rows without tasks are zero.
 template <typename T>
-__global__ void ttmc_fixup_kernel(const uint32_t* __restrict__ row_task, int J, const T* __restrict__ partial,
-                                  T* __restrict__ Y) {
+__global__ void ttmc_fixup_kernel(const uint32_t* __restrict__ row_task, const uint32_t* __restrict__ d_ntask,
+                                  uint32_t nwarps, int J, const T* __restrict__ partial, T* __restrict__ Y) {
+  const uint32_t per = (*d_ntask + nwarps - 1u) / nwarps;   // the task kernel's block size
   const int row = blockIdx.x;
   const uint32_t t0 = row_task[row], t1 = row_task[row + 1];
-  if (t1 - t0 == 1) return;
+  if (t1 > t0 && t0 / per == (t1 - 1) / per) return;
   for (int c = threadIdx.x; c < J; c += blockDim.x) {
     T s = T(0);
-    for (uint32_t t = t0; t < t1; ++t) s += partial[(size_t)t * J + c];
+    if (t1 > t0) {
+      s = partial[(size_t)t0 * J + c];
+      for (uint32_t h = (t0 / per + 1) * per; h < t1; h += per) s += partial[(size_t)h * J + c];
+    }
     Y[(size_t)row * J + c] = s;
   }
 }
@@ -375,8 +404,8 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, 32 * kW, smem, st>>>(a);
   MACH_LAUNCH_CHECK();
-  ttmc_fixup_kernel<T><<<L.nrows, 128, 0, st>>>(L.row_task, L.J, static_cast<const T*>(L.partial),
-                                                 static_cast<T*>(L.Y));
+  ttmc_fixup_kernel<T><<<L.nrows, 128, 0, st>>>(L.row_task, L.d_ntask, (uint32_t)(grid * kW), L.J,
+                                                 static_cast<const T*>(L.partial), static_cast<T*>(L.Y));
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
