@@ -146,6 +146,24 @@ def traffic_record(kernel: str):
 
 
 # ----------------------------------------------------------------------------
+# replicas: every rank decomposes its own tensor; the job's time is the
+# slowest rank's, the job's throughput all ranks' decompositions over it
+# ----------------------------------------------------------------------------
+def max_over_ranks(ms: float, world: int, device) -> float:
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps_per_rank: int, world: int, max_ms: float) -> float:
+    return world * steps_per_rank / (max_ms / 1e3)
+
+
+# ----------------------------------------------------------------------------
 # oracle timing (cpu_baseline and --impl reference): spawned subprocess
 # ----------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
@@ -431,11 +449,8 @@ def main():
     launches = lib.mach_launch_count() - launches0
     total_ms = e0.elapsed_time(e1)
     per_step = [a.elapsed_time(b) for a, b in step_ms]
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    value = replica_throughput(args.steps, world, total_ms)
 
     # per-kernel-class profile (library-recorded CUDA events on this stream)
     prof = {}
@@ -480,10 +495,8 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ems = f0.elapsed_time(f1)
-        et = torch.tensor([ems], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.e2e_steps / (float(et.item()) / 1e3), "unit": "decompositions/s",
+        ems = max_over_ranks(ems, world, "cuda")
+        e2e = {"value": replica_throughput(args.e2e_steps, world, ems), "unit": "decompositions/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         del host, xdev
 
