@@ -208,6 +208,66 @@ __device__ void chol_warp(T* G, int n, int* dead) {
   }
 }
 
+// The same factorisation register resident (one warp): lane i holds row i
+// of the Gram in NB registers; column j takes the pivot from lane j by a
+// shuffle, lane j scales its row into row j of R, and every later row i
+// subtracts R[j][i] R[j][:] (R[j][i] is lane i's own entry of the
+// symmetric Gram over the pivot).  Full rows are updated, so the Gram stays
+// symmetric.  R (upper) is written back to G.
+template <typename T, int NB>
+__device__ __noinline__ void chol_reg(T* G, int n, int* dead) {
+  const int lane = threadIdx.x & 31;
+  const T floor_piv = sizeof(T) == 8 ? T(1e-24) : T(1e-10);
+  T g[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) g[c] = (lane < n && c < n) ? G[lane * kLd + c] : T(0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < n) {
+      const T piv = __shfl_sync(0xffffffffu, g[j], j);
+      if (!(piv > floor_piv)) {
+        // a numerically dependent column: row j of R is e_j^T
+        if (lane == j) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) g[c] = c == j ? T(1) : T(0);
+        }
+        if (lane == 0) dead[j] = 1;
+      } else {
+        const T djj = sqrt(piv);
+        const T inv = T(1) / djj;
+        if (lane == j) {
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c > j) g[c] *= inv;
+          g[j] = djj;
+        }
+        if (lane == 0) dead[j] = 0;
+        const T rji = g[j] * inv;   // lane i > j: R[j][i]
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (c > j) {
+            const T rjc = __shfl_sync(0xffffffffu, g[c], j);
+            if (lane > j) g[c] -= rji * rjc;
+          }
+        }
+      }
+    }
+  }
+  if (lane < n) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < n) G[lane * kLd + c] = c >= lane ? g[c] : T(0);
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ void chol_fast(T* G, int n, int* dead) {
+  if (n <= 16) chol_reg<T, 16>(G, n, dead);
+  else if (n <= 24) chol_reg<T, 24>(G, n, dead);
+  else chol_reg<T, 32>(G, n, dead);
+}
+
 // Column scaling of a Gram: d_j = 1/sqrt(G_jj), or 0 for columns whose norm
 // is negligible against the largest one.
 template <typename T>
@@ -223,20 +283,47 @@ __device__ void col_scale_warp(const T* G, int n, T* d) {
 }
 
 // row[0..b) <- row D R^-1 for the upper factor R (shared memory, ld kLd)
-// of a rank-revealing Cholesky (dead columns zeroed).  Unrolled over the
-// kB columns so that the row stays in registers.
-template <typename T>
-__device__ __forceinline__ void solve_row(T (&row)[kB], const T* d, const T* R, const int* dead, int b) {
+// of a rank-revealing Cholesky (dead columns zeroed).  Unrolled over NB >= b
+// columns so that the row stays in registers; solve_row picks NB.
+template <typename T, int NB>
+__device__ __forceinline__ void solve_row_nb(T (&row)[kB], const T* d, const T* R, const int* dead, int b) {
 #pragma unroll
-  for (int j = 0; j < kB; ++j)
+  for (int j = 0; j < NB; ++j)
     if (j < b) row[j] *= d[j];
 #pragma unroll
-  for (int j = 0; j < kB; ++j) {
+  for (int j = 0; j < NB; ++j) {
     if (j < b) {
       T v = row[j];
 #pragma unroll
       for (int k = 0; k < j; ++k) v -= row[k] * R[k * kLd + j];
       row[j] = dead[j] ? T(0) : v / R[j * kLd + j];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void solve_row(T (&row)[kB], const T* d, const T* R, const int* dead, int b) {
+  if (b <= 16) solve_row_nb<T, 16>(row, d, R, dead, b);
+  else if (b <= 24) solve_row_nb<T, 24>(row, d, R, dead, b);
+  else solve_row_nb<T, 32>(row, d, R, dead, b);
+}
+
+// dst[i * ldd + j] = src[i * lds + j] for i < rows, j < cols: a CTA-wide
+// copy with 8 independent loads in flight per thread
+template <typename T>
+__device__ void stage_rows(T* dst, int ldd, const T* __restrict__ src, int lds, int rows, int cols) {
+  const int n = rows * cols, nthr = blockDim.x;
+  for (int o0 = threadIdx.x; o0 < n; o0 += 8 * nthr) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int o = o0 + u * nthr;
+      v[u] = o < n ? src[(size_t)(o / cols) * lds + (o - (o / cols) * cols)] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int o = o0 + u * nthr;
+      if (o < n) dst[(o / cols) * ldd + (o - (o / cols) * cols)] = v[u];
     }
   }
 }
@@ -329,7 +416,7 @@ __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev
     if (lane < b)
       for (int j = 0; j < b; ++j) s.F[lane * kLd + j] *= s.d[lane] * s.d[j];
     __syncwarp();
-    chol_warp<T>(s.F, b, s.dead);
+    chol_fast<T>(s.F, b, s.dead);
   }
   __syncthreads();
   // S <- S D R^-1: forward substitution against upper R, one row per thread
@@ -694,15 +781,12 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     V = reinterpret_cast<T*>(eig_smem);
     W = V + (size_t)M * ld;
     U = W + (size_t)M * ld;
-    // rows on warps, columns on lanes (coalesced, no division)
-    for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
-      for (int j = threadIdx.x & 31; j < b; j += 32) V[i * ld + j] = a.V[(size_t)i * b + j];
+    stage_rows<T>(V, ld, a.V, b, M, b);
   }
   if (smem_mode == 2) {
     T* Cs = U + (size_t)M * ld;
     ldc = M | 1;
-    for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
-      for (int k = threadIdx.x & 31; k < M; k += 32) Cs[i * ldc + k] = a.C[(size_t)i * M + k];
+    stage_rows<T>(Cs, ldc, a.C, M, M, M);
     C = Cs;
   }
   if (threadIdx.x == 0) prev = 1e300;
@@ -716,7 +800,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     if (lane < b)
       for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
     __syncwarp();
-    chol_warp<T>(bs.G, b, bs.dead);
+    chol_fast<T>(bs.G, b, bs.dead);
     // S = D R^-1 (upper): solve row by row of the identity scaled by D
     if (lane < b) {
       T row[kB];
@@ -909,7 +993,7 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
       if (lane < b)
         for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
       __syncwarp();
-      chol_warp<T>(bs.G, b, bs.dead);
+      chol_fast<T>(bs.G, b, bs.dead);
       if (lane < b) {
         T row[kB];
 #pragma unroll
