@@ -253,16 +253,30 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
     }
     phase_bits ^= 1u << cur;
 
+    // fibre metadata of batch k + 1 is loaded while batch k is processed:
+    // lane l holds fib_start / fib_mid of fibre fb + l, lane 31 also the
+    // start of the fibre after the batch (the end of its own fibre)
+    uint32_t fs_n, mid_n, fl_n = 0;
+    {
+      const uint32_t f = (uint32_t)tk.w + lane;
+      fs_n = f < nfib ? a.fib_start[f] : 0xffffffffu;
+      mid_n = f < nfib ? a.fib_mid[f] : 0u;
+      if (lane == 31 && f + 1 <= nfib) fl_n = a.fib_start[f + 1];
+    }
     for (uint32_t fb = (uint32_t)tk.w;; fb += 32) {
       const uint32_t f = fb + lane;
-      uint32_t fs = 0xffffffffu, fe = 0;
-      if (f < nfib) {
-        fs = a.fib_start[f];
-        fe = a.fib_start[f + 1];
-      }
+      const uint32_t fs = fs_n, mid_f = mid_n;
+      uint32_t fe = __shfl_down_sync(0xffffffffu, fs, 1);
+      if (lane == 31) fe = fl_n;
       const bool valid = f < nfib && fs < e1;
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       if (!vm) break;
+      {
+        const uint32_t fn = f + 32;
+        fs_n = fn < nfib ? a.fib_start[fn] : 0xffffffffu;
+        mid_n = fn < nfib ? a.fib_mid[fn] : 0u;
+        if (lane == 31 && fn + 1 <= nfib) fl_n = a.fib_start[fn + 1];
+      }
       T z[RLM];
 #pragma unroll
       for (int b = 0; b < RLM; ++b) z[b] = T(0);
@@ -270,14 +284,28 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
       if (valid) {
         const uint32_t s0 = (fs > e0 ? fs : e0) - base;
         const uint32_t s1 = (fe < e1 ? fe : e1) - base;
-        for (uint32_t e = s0; e < s1; ++e) {
-          const T v = (T)sval[e];
-          const T* ar = Aleaf + (size_t)sleaf[e] * rl;
+        if (rl == RLM && (RLM % 2) == 0 && sizeof(T) == 4) {
+          // exact even rank: 8-byte loads of the factor row
+          for (uint32_t e = s0; e < s1; ++e) {
+            const T v = (T)sval[e];
+            const float2* ar = reinterpret_cast<const float2*>(Aleaf + (size_t)sleaf[e] * RLM);
 #pragma unroll
-          for (int b = 0; b < RLM; ++b)
-            if (b < rl) z[b] += v * ar[b];
+            for (int b = 0; b < RLM / 2; ++b) {
+              const float2 w2 = ar[b];
+              z[2 * b] += v * (T)w2.x;
+              z[2 * b + 1] += v * (T)w2.y;
+            }
+          }
+        } else {
+          for (uint32_t e = s0; e < s1; ++e) {
+            const T v = (T)sval[e];
+            const T* ar = Aleaf + (size_t)sleaf[e] * rl;
+#pragma unroll
+            for (int b = 0; b < RLM; ++b)
+              if (b < rl) z[b] += v * ar[b];
+          }
         }
-        mid = a.fib_mid[f];
+        mid = mid_f;
       }
 #pragma unroll
       for (int b = 0; b < RLM; ++b)
