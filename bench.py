@@ -475,6 +475,24 @@ def main():
                 "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
                 "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
 
+    # the sector-skipping sampler on the same resident input (outside the timed
+    # region): its time, and the share of X's 32-byte sectors it has to read
+    skip = None
+    if w.spec.dtype in ("float32", "float64"):
+        lib.mach_profile_enable(1)
+        for _ in range(3):
+            s2 = mach.sample(X, w.p, spec_r.seed, skip=True)
+            s2.free()
+        ms2 = mach.ctypes.c_double()
+        n2 = mach.ctypes.c_int64()
+        by2 = mach.ctypes.c_double()
+        lib.mach_profile_query(0, mach.ctypes.byref(ms2), mach.ctypes.byref(n2), mach.ctypes.byref(by2))
+        lib.mach_profile_enable(0)
+        per = 4 if w.spec.dtype == "float32" else 8
+        skip = {"ms": ms2.value / max(n2.value, 1), "sector_fraction_read": 1.0 - (1.0 - w.p) ** (32 // per),
+                "vs_dense": samp["ms"] / max(samp["launches"], 1) / (ms2.value / max(n2.value, 1))
+                if ms2.value else None}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -516,7 +534,7 @@ def main():
                 "data": "synthetic", "config": config_dict(w, prec),
                 "p50_ms": statistics.median(per_step),
                 "p99_ms": sorted(per_step)[max(0, math.ceil(0.99 * len(per_step)) - 1)],
-                "sampler_gbs": samp_gbs, "sampler_frac_of_hbm": samp_gbs / hbm_peak,
+                "sampler_gbs": samp_gbs, "sampler_frac_of_hbm": samp_gbs / hbm_peak, "sampler_skip": skip,
                 "roofline": roofline, "profile_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "eigensolver": last_stats}

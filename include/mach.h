@@ -107,6 +107,19 @@ mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_
                         double p, uint64_t seed, void* stream, mach_sample_t* out);
 
 /* ---------------------------------------------------------------------------
+ * mach_sample_skip — mach_sample for an input resident in device memory,
+ * reading only what the coin keeps.  The coin depends on the index alone
+ * (Section 3 Remark 1), so the kept entries are known before X is read:
+ * only the 32-byte sectors that hold kept entries are fetched, i.e.
+ * 1 - (1 - p)^(32 / s_in) of X (7.7 % of an FP32 tensor at p = 0.01) instead
+ * of all of it.  Same arguments, same kept set and orderings, same errors
+ * as mach_sample.  The paper samples a stream it reads once in full; this
+ * form is for data already in HBM.
+ */
+mach_status mach_sample_skip(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims,
+                             double p, uint64_t seed, void* stream, mach_sample_t* out);
+
+/* ---------------------------------------------------------------------------
  * mach_sample_noalloc — the same coin and compaction as mach_sample (Section
  * 3 Remark 1; Algorithm 1 and 2, first block), written straight into
  * caller-owned buffers, with NO allocation of any kind: no device or host

@@ -315,8 +315,8 @@ mach_status mach_profile_query(int kind, double* total_ms, int64_t* launches, do
 
 int64_t mach_launch_count(void) { return (int64_t)g_launches.load(); }
 
-mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p, uint64_t seed,
-                        void* stream, mach_sample_t* out) {
+static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p, uint64_t seed,
+                               void* stream, mach_sample_t* out, bool skip) {
   if (!x_dev || !dims || !out) return MACH_EINVAL;
   if (d < 2 || d > kMaxModes) return MACH_EINVAL;
   if (dtype != MACH_F32 && dtype != MACH_F64) return MACH_EINVAL;
@@ -368,7 +368,7 @@ mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_
     if ((s = dev_alloc(seg_cnt, (size_t)pl.nseg * 8, st)) != MACH_OK) return fail(s);
     prof_begin(PROF_SAMPLER, st);
     if ((s = launch_sampler_seg(x_dev, dtype, N, seed, h->T, pl, static_cast<int64_t*>(seg_idx.ptr), seg_val.ptr,
-                                static_cast<int64_t*>(seg_cnt.ptr), &ds->err, st)) != MACH_OK)
+                                static_cast<int64_t*>(seg_cnt.ptr), &ds->err, st, skip)) != MACH_OK)
       return fail(s);
     if ((s = launch_seg_gather(dtype, pl, static_cast<const int64_t*>(seg_cnt.ptr),
                                static_cast<const int64_t*>(seg_idx.ptr), seg_val.ptr,
@@ -490,6 +490,16 @@ mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_
   }
   *out = h;
   return MACH_OK;
+}
+
+mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p, uint64_t seed,
+                        void* stream, mach_sample_t* out) {
+  return sample_impl(x_dev, dtype, d, dims, p, seed, stream, out, false);
+}
+
+mach_status mach_sample_skip(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p,
+                             uint64_t seed, void* stream, mach_sample_t* out) {
+  return sample_impl(x_dev, dtype, d, dims, p, seed, stream, out, true);
 }
 
 mach_status mach_sample_count(mach_sample_t s, int64_t* n_kept) {

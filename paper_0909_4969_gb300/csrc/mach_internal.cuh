@@ -276,7 +276,7 @@ struct SegPlan {
 SegPlan plan_segments(int64_t n, mach_dtype dt, double q);
 mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
                                int64_t* seg_idx, void* seg_val, int64_t* seg_count, unsigned* d_err,
-                               cudaStream_t st);
+                               cudaStream_t st, bool skip);
 mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const int64_t* seg_idx,
                               const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
                               cudaStream_t st);

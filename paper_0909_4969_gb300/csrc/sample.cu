@@ -372,7 +372,10 @@ struct SegArgs {
   unsigned* err;
 };
 
-template <typename V>
+// SKIP (the sector-skipping form, for HBM-resident inputs): no staging; the
+// kept values are read directly, so only the 32-byte sectors that hold kept
+// entries leave HBM (1 - (1 - p)^(32 / s_in) of X), the same kept set.
+template <typename V, bool SKIP>
 __global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
   using C = SampCfg<V>;
   static_assert(C::kTile == kSegThreads * C::kEPT, "tile layout");
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
       mbar_arrive(&bar[s]);
     }
   };
-  if (tid == 0)
+  if (!SKIP && tid == 0)
     for (int s = 0; s < kSegStages && t0 + s < t1; ++s) issue(t0 + s, s);
   int64_t* out_idx = a.seg_idx + (size_t)blockIdx.x * a.seg_cap;
   V* out_val = static_cast<V*>(a.seg_val) + (size_t)blockIdx.x * a.seg_cap;
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
       if (lane >= o) incl += y;
     }
     if (lane == 31) warp_tot[warp] = incl;
-    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(j / kSegStages) & 1u);
+    const bool ok = SKIP || mbar_wait_bounded(&bar[s], (uint32_t)(j / kSegStages) & 1u);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(a.err, DEV_TIMEOUT);
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
         mask &= mask - 1;
         const int64_t l = e_thr + b;
         const int64_t in_tile = l - e_tile;
-        const V v = in_tile < n_staged ? buf[in_tile] : x[l];
+        const V v = (!SKIP && in_tile < n_staged) ? buf[in_tile] : __ldg(x + l);
         if (pos < a.seg_cap) {
           out_idx[pos] = l;
           out_val[pos] = v;
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
     }
     base += blk;
     __syncthreads();   // stage s and warp_tot are free again
-    if (tid == 0 && t + kSegStages < t1) issue(t + kSegStages, s);
+    if (!SKIP && tid == 0 && t + kSegStages < t1) issue(t + kSegStages, s);
   }
   if (tid == 0) a.seg_count[blockIdx.x] = base;
 }
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restri
   }
 }
 
-template <typename V>
+template <typename V, bool SKIP>
 mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl, int64_t* seg_idx,
                          void* seg_val, int64_t* seg_count, unsigned* d_err, cudaStream_t st) {
   using C = SampCfg<V>;
@@ -532,9 +535,9 @@ mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, co
   a.seg_val = seg_val;
   a.seg_count = seg_count;
   a.err = d_err;
-  const size_t smem = kSegStages * C::kStageBytes;
-  MACH_TRY(allow_max_dyn_smem(sample_seg_kernel<V>));
-  sample_seg_kernel<V><<<(unsigned)pl.nseg, kSegThreads, smem, st>>>(a);
+  const size_t smem = SKIP ? 0 : kSegStages * C::kStageBytes;
+  MACH_TRY(allow_max_dyn_smem(sample_seg_kernel<V, SKIP>));
+  sample_seg_kernel<V, SKIP><<<(unsigned)pl.nseg, kSegThreads, smem, st>>>(a);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
@@ -558,9 +561,12 @@ SegPlan plan_segments(int64_t n, mach_dtype dt, double q) {
 
 mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
                                int64_t* seg_idx, void* seg_val, int64_t* seg_count, unsigned* d_err,
-                               cudaStream_t st) {
-  if (dt == MACH_F32) return launch_seg_t<float>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
-  return launch_seg_t<double>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
+                               cudaStream_t st, bool skip) {
+  if (dt == MACH_F32)
+    return skip ? launch_seg_t<float, true>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st)
+                : launch_seg_t<float, false>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
+  return skip ? launch_seg_t<double, true>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st)
+              : launch_seg_t<double, false>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
 }
 
 mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const int64_t* seg_idx,

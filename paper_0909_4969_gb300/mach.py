@@ -35,6 +35,8 @@ SIGNATURES = {
     "mach_sample_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                            _c_i64p, ctypes.c_void_p]),
+    "mach_sample_skip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
+                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "mach_sample_count": (ctypes.c_int, [ctypes.c_void_p, _c_i64p]),
     "mach_sample_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "mach_sample_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -135,7 +137,8 @@ def colmajor(A: torch.Tensor) -> torch.Tensor:
 class Sample:
     """A sampled tensor (mach_sample_t) owning its device buffers."""
 
-    def __init__(self, x: torch.Tensor, p: float, seed: int, stream=None):
+    def __init__(self, x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False):
+        """skip=True: mach_sample_skip (reads only the sectors holding kept entries)."""
         if not x.is_cuda or not x.is_contiguous():
             raise ValueError("x must be a contiguous CUDA tensor")
         lib = load()
@@ -147,9 +150,9 @@ class Sample:
         self.dtype = x.dtype
         self.device = x.device
         h = ctypes.c_void_p()
-        _check("mach_sample", lib.mach_sample(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), self.d,
-                                              _i64(self.dims), self.p, ctypes.c_uint64(self.seed),
-                                              _stream(stream), ctypes.byref(h)))
+        fn = lib.mach_sample_skip if skip else lib.mach_sample
+        _check("mach_sample", fn(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), self.d, _i64(self.dims), self.p,
+                                 ctypes.c_uint64(self.seed), _stream(stream), ctypes.byref(h)))
         self._h = h
 
     @property
@@ -224,8 +227,8 @@ class Sample:
             pass
 
 
-def sample(x: torch.Tensor, p: float, seed: int, stream=None) -> Sample:
-    return Sample(x, p, seed, stream)
+def sample(x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False) -> Sample:
+    return Sample(x, p, seed, stream, skip)
 
 
 def sample_noalloc(x: torch.Tensor, p: float, seed: int, idx_out: torch.Tensor, val_out: torch.Tensor,

@@ -12,6 +12,7 @@ from tests._gpu import mach_module, torch
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("skip", [False, True])
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
 @pytest.mark.parametrize("dims,p,seed", [
     ((100, 50, 200), 0.1, 0),          # small FP64 workload shape, many tiles
@@ -21,12 +22,13 @@ pytestmark = pytest.mark.gpu
     ((41, 17, 23, 11), 0.05, 2 ** 40 + 17),   # 4-way, seed with a high word
     ((300, 250, 190), 0.01, 123),      # sparse, ~14k kept over 14.25M entries
 ])
-def test_sample_bit_exact(dims, p, seed, dtype):
+def test_sample_bit_exact(dims, p, seed, dtype, skip):
+    """mach_sample and its sector-skipping form mach_sample_skip."""
     mach = mach_module()
     rng = np.random.default_rng(0)
     X = rng.standard_normal(dims).astype(dtype)
     xd = torch.from_numpy(X).cuda()
-    s = mach.sample(xd, p, seed)
+    s = mach.sample(xd, p, seed, skip=skip)
     idx = s.indices().cpu().numpy()
     vals = s.values().cpu().numpy()
     ref = O.kept_indices(0, X.size, p, seed)
@@ -94,6 +96,11 @@ def test_sample_full_size_windows():
         got = vals_h[lo:hi]
         want = X.reshape(-1)[torch.from_numpy(ref).cuda()].cpu().numpy() if ref.size else got
         assert np.array_equal(got, want)
+    # the sector-skipping form keeps exactly the same (index, value) list
+    s2 = mach.sample(X, w.p, w.spec.seed, skip=True)
+    assert torch.equal(s2.indices(), idx)
+    assert torch.equal(s2.values(), s.values())
+    s2.free()
     s.free()
     del X
     torch.cuda.empty_cache()
