@@ -353,25 +353,25 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
   if ((s = dev_alloc(h->scal, sizeof(SampleScalars), st)) != MACH_OK) return fail(s);
   SampleScalars* ds = h->dscal();
   if (cudaMemsetAsync(ds, 0, sizeof(SampleScalars), st) != cudaSuccess) return fail(MACH_ECUDA);
-  // coin + compaction: per-CTA segments, then an ordered gather into idx / val
+  // coin + compaction: per-warp segments, then an ordered gather into idx / val
   // (sized for the segments' capacity, so no host round trip in between)
   const double q = h->T >= (1ull << 32) ? 1.0 : (double)h->T / 4294967296.0;
   SegPlan pl = plan_segments(N, dtype, q);
   const size_t vs = dtype_size(dtype);
   for (int attempt = 0; attempt < 2; ++attempt) {
-    DevBuf seg_idx, seg_val, seg_cnt;
+    DevBuf seg_off, seg_val, seg_cnt;
     const int64_t cap_all = pl.nseg * pl.seg_cap;
     if ((s = dev_alloc(h->idx, (size_t)cap_all * 8, st)) != MACH_OK) return fail(s);
     if ((s = dev_alloc(h->val, (size_t)cap_all * vs, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(seg_idx, (size_t)cap_all * 8, st)) != MACH_OK) return fail(s);
+    if ((s = dev_alloc(seg_off, (size_t)cap_all * 4, st)) != MACH_OK) return fail(s);
     if ((s = dev_alloc(seg_val, (size_t)cap_all * vs, st)) != MACH_OK) return fail(s);
     if ((s = dev_alloc(seg_cnt, (size_t)pl.nseg * 8, st)) != MACH_OK) return fail(s);
     prof_begin(PROF_SAMPLER, st);
-    if ((s = launch_sampler_seg(x_dev, dtype, N, seed, h->T, pl, static_cast<int64_t*>(seg_idx.ptr), seg_val.ptr,
-                                static_cast<int64_t*>(seg_cnt.ptr), &ds->err, st, skip)) != MACH_OK)
+    if ((s = launch_sampler_seg(x_dev, dtype, N, seed, h->T, pl, static_cast<uint32_t*>(seg_off.ptr), seg_val.ptr,
+                                static_cast<int64_t*>(seg_cnt.ptr), st, skip)) != MACH_OK)
       return fail(s);
     if ((s = launch_seg_gather(dtype, pl, static_cast<const int64_t*>(seg_cnt.ptr),
-                               static_cast<const int64_t*>(seg_idx.ptr), seg_val.ptr,
+                               static_cast<const uint32_t*>(seg_off.ptr), seg_val.ptr,
                                static_cast<int64_t*>(h->idx.ptr), h->val.ptr, cap_all, &ds->err, st)) != MACH_OK)
       return fail(s);
     prof_end(PROF_SAMPLER, st, 0.0);
@@ -383,7 +383,7 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
       set_last_error("sampler: %s", cudaGetErrorString(cudaGetLastError()));
       return fail(MACH_ECUDA);
     }
-    dev_free(seg_idx, st);
+    dev_free(seg_off, st);
     dev_free(seg_val, st);
     dev_free(seg_cnt, st);
     if (hs.err & DEV_TIMEOUT) return fail(MACH_ETIMEOUT);

@@ -97,6 +97,55 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
   return make_uint4(x0, x1, x2, x3);
 }
 
+// The same generator with the key schedule supplied by the launch
+// (k0[r] = key0 + r W0, k1[r] = key1 + r W1, mod 2^32), so the per-round key
+// bumps leave the integer pipe; counter words 2 and 3 are zero, so round 0
+// has one product.  Returns the same words as philox4x32_10.
+struct PhiloxSched {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+inline PhiloxSched make_philox_sched(uint64_t seed) {
+  PhiloxSched ks;
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    ks.k0[r] = k0;
+    ks.k1[r] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return ks;
+}
+
+// Both halves of the 32 x 32 -> 64-bit product, written as separate
+// mul.hi / mul.lo (measured on sm_103a: the form that leaves the integer
+// multiply pipe with the product work only).
+__device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t x, uint32_t& hi, uint32_t& lo) {
+  asm("mul.hi.u32 %0, %1, %2;" : "=r"(hi) : "r"(x), "r"(m));
+  asm("mul.lo.u32 %0, %1, %2;" : "=r"(lo) : "r"(x), "r"(m));
+}
+
+__device__ __forceinline__ uint4 philox4x32_10_sched(uint32_t c0, uint32_t c1, const PhiloxSched& ks) {
+  uint32_t h, l;
+  mul_hilo(kPhiloxM0, c0, h, l);
+  uint32_t x0 = c1 ^ ks.k0[0];
+  uint32_t x1 = 0u;
+  uint32_t x2 = h ^ ks.k1[0];
+  uint32_t x3 = l;
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_hilo(kPhiloxM0, x0, hi0, lo0);
+    mul_hilo(kPhiloxM1, x2, hi1, lo1);
+    x0 = hi1 ^ x1 ^ ks.k0[r];
+    x1 = lo1;
+    x2 = hi0 ^ x3 ^ ks.k1[r];
+    x3 = lo0;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
 // ----------------------------------------------------------------------------
 // Division of 64-bit unsigned integers by a run-time invariant divisor using
 // one multiply-high, after Granlund & Montgomery, "Division by invariant
@@ -270,14 +319,13 @@ int64_t sampler_scratch_words(int64_t n, mach_dtype dt);
 // pairs of its contiguous tiles into its own segment; then an ordered gather.
 struct SegPlan {
   int64_t nseg = 0;
-  int64_t tiles_per_cta = 0;
+  int64_t chunks_per_seg = 0;
   int64_t seg_cap = 0;
 };
 SegPlan plan_segments(int64_t n, mach_dtype dt, double q);
 mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
-                               int64_t* seg_idx, void* seg_val, int64_t* seg_count, unsigned* d_err,
-                               cudaStream_t st, bool skip);
-mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const int64_t* seg_idx,
+                               uint32_t* seg_off, void* seg_val, int64_t* seg_count, cudaStream_t st, bool skip);
+mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const uint32_t* seg_off,
                               const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
                               cudaStream_t st);
 // Fixed scratch of the allocation-free sampler (sample.cu): its size in

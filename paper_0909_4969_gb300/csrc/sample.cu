@@ -3,18 +3,18 @@
 // whether the entry is kept; kept (l, value) pairs are compacted in increasing
 // l.  The coin is value-independent, so the dense input is streamed once.
 //
-// GB300 design: a persistent, warp-specialised kernel.  Per CTA one control
-// warp claims 16 KiB tiles of X (one atomic counter, so claim order is tile
-// order), starts their 1-D TMA bulk copies into a 4-stage shared-memory ring
-// and runs the decoupled look-back; eight compute warps evaluate Philox for
-// each claimed tile as soon as it is claimed (16 FP32 / 8 FP64 consecutive
-// entries per thread), scan the keep counts inside the tile, and, once the
-// tile's global offset is known and its bytes have landed, write the kept
-// (l, value) pairs in order.  Stages are handed between the warps with
-// mbarriers.  Compute counts tile j while the control warp looks back for
-// tile j-1 and the writes of tile j-2 proceed; a stage is refilled only
-// after the following tile's look-back, so no warp waits on a look-back.
-// Philox is evaluated exactly once per counter; every wait is bounded.
+// Two kernels.  The product path of mach_sample (sample_seg_kernel, below)
+// gives every warp its own contiguous segment of X and concatenates the
+// segments afterwards, so no warp ever waits for another.  The decoupled
+// look-back kernel (sample_kernel, first) writes final positions directly
+// and needs only a small fixed scratch, which suits the allocation-free
+// entry point: per CTA one control warp claims 16 KiB tiles of X (one
+// atomic counter, so claim order is tile order), starts their 1-D TMA bulk
+// copies into a 4-stage shared-memory ring and runs the look-back; eight
+// compute warps evaluate Philox for each claimed tile, scan the keep counts
+// inside the tile, and, once the tile's global offset is known and its
+// bytes have landed, write the kept (l, value) pairs in order.  Every wait
+// is bounded.
 #include "mach_internal.cuh"
 
 #include <cmath>
@@ -345,150 +345,133 @@ mach_status launch_sampler_t(const void* x, int64_t n, uint64_t seed, uint64_t T
 }
 
 // ----------------------------------------------------------------------------
-// Segmented sampler (the product path of mach_sample).  Each CTA owns a
-// contiguous range of tiles and writes its kept (l, value) pairs, in
-// increasing l, into its own segment of a staging buffer; seg_gather_kernel
-// then concatenates the segments in CTA order, which is increasing l
-// overall.  No CTA ever waits for another.  Per tile the coin is evaluated
-// before the tile's bytes are waited for (it depends on l only), so the
-// Philox arithmetic overlaps the TMA stream of the 3-stage ring; 4 CTAs of
-// 8 warps per SM keep the integer pipes busy.
+// Segmented sampler (the product path of mach_sample).  Every warp owns a
+// contiguous range of 2048-entry chunks of X and works alone.  Lane 0 keeps
+// the chunk D ahead in flight from HBM into L2 with one bulk prefetch
+// (cp.async.bulk.prefetch.L2), so X crosses HBM exactly once; the lanes
+// evaluate the coin of their 64 consecutive entries (16 Philox calls, the
+// key schedule comes with the launch), scan the keep counts with warp
+// shuffles, and read only the kept values (from L2) while writing the kept
+// (offset in the segment, value) pairs, in increasing l, into the warp's own
+// segment of a staging buffer; seg_gather_kernel then concatenates the
+// segments in warp order and restores l.  No shared memory, no block barrier and no wait on another warp:
+// occupancy is set by registers alone, which keeps the integer pipes that
+// carry Philox busy.
 // ----------------------------------------------------------------------------
-constexpr int kSegThreads = 256;
-constexpr int kSegStages = 3;
+constexpr int kSegWarps = 8;
+constexpr int kSegThreads = 32 * kSegWarps;
+constexpr int kSegCtasPerSm = 4;
+constexpr int kCallsPerLane = 16;
+constexpr int kEntriesPerLane = 4 * kCallsPerLane;       // 64
+constexpr int kChunk = 32 * kEntriesPerLane;             // 2048 entries per chunk
+constexpr int kPrefetchAhead = 1;                        // chunks in flight per warp (more thrashes L2 at large p)
 
 struct SegArgs {
   const void* x;
   int64_t n;
-  uint32_t key0, key1;
+  PhiloxSched ks;
   uint32_t t32;
   int keep_all;
-  int64_t num_tiles;
-  int64_t tiles_per_cta;
+  int64_t num_chunks;
+  int64_t chunks_per_seg;
+  int64_t nseg;
   int64_t seg_cap;
-  int64_t* seg_idx;
+  uint32_t* seg_off;    // l - (first entry of the segment); a segment spans < 2^32 entries
   void* seg_val;
   int64_t* seg_count;
-  unsigned* err;
 };
 
-// SKIP (the sector-skipping form, for HBM-resident inputs): no staging; the
-// kept values are read directly, so only the 32-byte sectors that hold kept
-// entries leave HBM (1 - (1 - p)^(32 / s_in) of X), the same kept set.
-template <typename V, bool SKIP>
-__global__ void __launch_bounds__(kSegThreads, 4) sample_seg_kernel(SegArgs a) {
-  using C = SampCfg<V>;
-  static_assert(C::kTile == kSegThreads * C::kEPT, "tile layout");
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  V* stage = reinterpret_cast<V*>(smem_raw);
-  __shared__ uint64_t bar[kSegStages];
-  __shared__ int warp_tot[kSegThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const V* x = static_cast<const V*>(a.x);
-  const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_cta;
-  const int64_t t1 = min(a.num_tiles, t0 + a.tiles_per_cta);
-  if (tid == 0) {
-    for (int s = 0; s < kSegStages; ++s) mbar_init(&bar[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  // thread 0: bulk copy of tile t into stage s (16-byte-floored length; a
-  // ragged tail is read directly)
-  auto issue = [&](int64_t t, int s) {
-    const int64_t e0 = t * C::kTile;
-    const int64_t ne = min((int64_t)C::kTile, a.n - e0);
-    const uint32_t bytes = (uint32_t)(((uint64_t)ne * sizeof(V)) & ~(uint64_t)15);
-    fence_proxy_async_smem();
-    if (bytes) {
-      mbar_arrive_expect_tx(&bar[s], bytes);
-      bulk_g2s(stage + (size_t)s * C::kTile, x + e0, bytes, &bar[s]);
-    } else {
-      mbar_arrive(&bar[s]);
-    }
-  };
-  if (!SKIP && tid == 0)
-    for (int s = 0; s < kSegStages && t0 + s < t1; ++s) issue(t0 + s, s);
-  int64_t* out_idx = a.seg_idx + (size_t)blockIdx.x * a.seg_cap;
-  V* out_val = static_cast<V*>(a.seg_val) + (size_t)blockIdx.x * a.seg_cap;
-  int64_t base = 0;
-  int j = 0;
-  for (int64_t t = t0; t < t1; ++t, ++j) {
-    const int s = j % kSegStages;
-    // the coin of this thread's entries (no data needed)
-    const int64_t e_thr = t * C::kTile + (int64_t)tid * C::kEPT;
-    const uint64_t q0 = (uint64_t)e_thr >> 2;
-    uint32_t mask = 0;
+__device__ __forceinline__ void prefetch_l2_bulk(const void* g, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
+}
+
+// Keep bits of 8 Philox calls (32 consecutive entries from counter q_lo | k0).
+__device__ __forceinline__ uint32_t coin_bits8(uint32_t q_lo, uint32_t q_hi, int k0, const SegArgs& a) {
+  uint32_t m = 0;
 #pragma unroll
-    for (int c = 0; c < C::kCPT; ++c) {
-      const uint64_t q = q0 + c;
-      const uint4 w = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), a.key0, a.key1);
-      uint32_t b;
-      if (a.keep_all) {
-        b = 0xFu;
-      } else {
-        b = (uint32_t)(w.x < a.t32) | ((uint32_t)(w.y < a.t32) << 1) | ((uint32_t)(w.z < a.t32) << 2) |
-            ((uint32_t)(w.w < a.t32) << 3);
-      }
-      mask |= b << (4 * c);
+  for (int k = 0; k < 8; ++k) {
+    const uint4 w = philox4x32_10_sched(q_lo | (uint32_t)(k0 + k), q_hi, a.ks);
+    const uint32_t b = (uint32_t)(w.x < a.t32) | ((uint32_t)(w.y < a.t32) << 1) |
+                       ((uint32_t)(w.z < a.t32) << 2) | ((uint32_t)(w.w < a.t32) << 3);
+    m |= b << (4 * k);
+  }
+  return m;
+}
+
+// STREAM: prefetch every chunk into L2 (the one-pass form, X crosses HBM
+// once).  Without it (the sector-skipping form, for HBM-resident inputs)
+// only the 32-byte sectors that hold kept entries leave HBM
+// (1 - (1 - p)^(32 / s_in) of X); the kept set is the same.
+template <typename V, bool STREAM>
+__global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm) sample_seg_kernel(SegArgs a) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t seg = (int64_t)blockIdx.x * kSegWarps + warp;
+  if (seg >= a.nseg) return;
+  const V* x = static_cast<const V*>(a.x);
+  const int64_t c0 = seg * a.chunks_per_seg;
+  const int64_t c1 = min(a.num_chunks, c0 + a.chunks_per_seg);
+  auto prefetch = [&](int64_t c) {
+    const int64_t e0 = c * kChunk;
+    const int64_t ne = min((int64_t)kChunk, a.n - e0);
+    const uint32_t bytes = (uint32_t)(((uint64_t)ne * sizeof(V)) & ~(uint64_t)15);
+    if (bytes) prefetch_l2_bulk(x + e0, bytes);
+  };
+  if (STREAM && lane == 0)
+    for (int d = 0; d < kPrefetchAhead && c0 + d < c1; ++d) prefetch(c0 + d);
+  uint32_t* out_off = a.seg_off + (size_t)seg * a.seg_cap;
+  V* out_val = static_cast<V*>(a.seg_val) + (size_t)seg * a.seg_cap;
+  const V* x_seg = x + c0 * kChunk;
+  const uint32_t cap = (uint32_t)a.seg_cap;
+  uint32_t base = 0;
+  for (int64_t c = c0; c < c1; ++c) {
+    if (STREAM && lane == 0 && c + kPrefetchAhead < c1) prefetch(c + kPrefetchAhead);
+    const int64_t e_lane = c * kChunk + (int64_t)lane * kEntriesPerLane;
+    // q0 = e_lane / 4 is a multiple of 16, so the lane's 16 counters differ
+    // in the low word only
+    const uint64_t q0 = (uint64_t)e_lane >> 2;
+    const uint32_t q_lo = (uint32_t)q0, q_hi = (uint32_t)(q0 >> 32);
+    uint64_t mask;
+    if (a.keep_all) {
+      mask = ~0ull;
+    } else {
+      const uint32_t lo = coin_bits8(q_lo, q_hi, 0, a);
+      const uint32_t hi = coin_bits8(q_lo, q_hi, 8, a);
+      mask = ((uint64_t)hi << 32) | lo;
     }
-    const int64_t valid = a.n - e_thr;
-    if (valid < C::kEPT) mask &= valid <= 0 ? 0u : ((1u << valid) - 1u);
-    const int cnt = __popc(mask);
+    if (c == a.num_chunks - 1) {
+      const int64_t valid = a.n - e_lane;
+      if (valid < kEntriesPerLane) mask &= valid <= 0 ? 0ull : ((1ull << valid) - 1ull);
+    }
+    const int cnt = __popcll(mask);
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    if (lane == 31) warp_tot[warp] = incl;
-    const bool ok = SKIP || mbar_wait_bounded(&bar[s], (uint32_t)(j / kSegStages) & 1u);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(a.err, DEV_TIMEOUT);
-        for (int q = 1; q < kSegStages; ++q)
-          if (t + q < t1) (void)mbar_wait_bounded(&bar[(j + q) % kSegStages], (uint32_t)((j + q) / kSegStages) & 1u);
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t pos = base + (uint32_t)(incl - cnt);
+    const uint32_t off_lane = (uint32_t)((c - c0) * kChunk) + (uint32_t)(lane * kEntriesPerLane);
+    while (mask) {
+      const uint32_t off = off_lane + (uint32_t)(__ffsll((long long)mask) - 1);
+      mask &= mask - 1;
+      if (pos < cap) {
+        out_off[pos] = off;
+        out_val[pos] = __ldg(x_seg + off);
       }
-      return;
+      ++pos;
     }
-    int warp_off = 0, blk = 0;
-#pragma unroll
-    for (int w = 0; w < kSegThreads / 32; ++w) {
-      const int v = warp_tot[w];
-      warp_off += (w < warp) ? v : 0;
-      blk += v;
-    }
-    if (mask) {
-      const V* buf = stage + (size_t)s * C::kTile;
-      const int64_t e_tile = t * C::kTile;
-      const int64_t tile_n = min((int64_t)C::kTile, a.n - e_tile);
-      const int64_t n_staged = (int64_t)((((uint64_t)tile_n * sizeof(V)) & ~(uint64_t)15) / sizeof(V));
-      int64_t pos = base + warp_off + incl - cnt;
-      while (mask) {
-        const int b = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int64_t l = e_thr + b;
-        const int64_t in_tile = l - e_tile;
-        const V v = (!SKIP && in_tile < n_staged) ? buf[in_tile] : __ldg(x + l);
-        if (pos < a.seg_cap) {
-          out_idx[pos] = l;
-          out_val[pos] = v;
-        }
-        ++pos;
-      }
-    }
-    base += blk;
-    __syncthreads();   // stage s and warp_tot are free again
-    if (!SKIP && tid == 0 && t + kSegStages < t1) issue(t + kSegStages, s);
+    base += (uint32_t)tot;
   }
-  if (tid == 0) a.seg_count[blockIdx.x] = base;
+  if (lane == 0) a.seg_count[seg] = base;
 }
 
-// Concatenate the segments in CTA order into idx / val[0, K); block c
+// Concatenate the segments in warp order into idx / val[0, K); block c
 // copies segment c.  Segments that overflowed their capacity are flagged
 // (the host then reruns with the exact capacity).
 template <typename V>
 __global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restrict__ seg_count, int64_t seg_cap,
-                                                         const int64_t* __restrict__ seg_idx,
+                                                         int64_t seg_span, const uint32_t* __restrict__ seg_off,
                                                          const V* __restrict__ seg_val, int64_t* __restrict__ idx,
                                                          V* __restrict__ val, int64_t out_cap, unsigned* err) {
   __shared__ int64_t off;
@@ -509,35 +492,33 @@ __global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restri
     if (threadIdx.x == 0) atomicOr(err, DEV_OVERFLOW);
     return;
   }
-  const int64_t* si = seg_idx + (size_t)c * seg_cap;
+  const int64_t l0 = (int64_t)c * seg_span;
+  const uint32_t* so = seg_off + (size_t)c * seg_cap;
   const V* sv = seg_val + (size_t)c * seg_cap;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    idx[off + i] = si[i];
+    idx[off + i] = l0 + so[i];
     val[off + i] = sv[i];
   }
 }
 
-template <typename V, bool SKIP>
-mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl, int64_t* seg_idx,
-                         void* seg_val, int64_t* seg_count, unsigned* d_err, cudaStream_t st) {
-  using C = SampCfg<V>;
+template <typename V, bool STREAM>
+mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl, uint32_t* seg_off,
+                         void* seg_val, int64_t* seg_count, cudaStream_t st) {
   SegArgs a;
   a.x = x;
   a.n = n;
-  a.key0 = (uint32_t)(seed & 0xffffffffu);
-  a.key1 = (uint32_t)(seed >> 32);
+  a.ks = make_philox_sched(seed);
   a.keep_all = T >= (1ull << 32) ? 1 : 0;
   a.t32 = a.keep_all ? 0xffffffffu : (uint32_t)T;
-  a.num_tiles = ceil_div(n, C::kTile);
-  a.tiles_per_cta = pl.tiles_per_cta;
+  a.num_chunks = ceil_div(n, kChunk);
+  a.chunks_per_seg = pl.chunks_per_seg;
+  a.nseg = pl.nseg;
   a.seg_cap = pl.seg_cap;
-  a.seg_idx = seg_idx;
+  a.seg_off = seg_off;
   a.seg_val = seg_val;
   a.seg_count = seg_count;
-  a.err = d_err;
-  const size_t smem = SKIP ? 0 : kSegStages * C::kStageBytes;
-  MACH_TRY(allow_max_dyn_smem(sample_seg_kernel<V, SKIP>));
-  sample_seg_kernel<V, SKIP><<<(unsigned)pl.nseg, kSegThreads, smem, st>>>(a);
+  const int64_t grid = ceil_div(pl.nseg, kSegWarps);
+  sample_seg_kernel<V, STREAM><<<(unsigned)grid, kSegThreads, 0, st>>>(a);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
@@ -545,39 +526,40 @@ mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, co
 }  // namespace
 
 SegPlan plan_segments(int64_t n, mach_dtype dt, double q) {
-  const int64_t tile = dt == MACH_F32 ? SampCfg<float>::kTile : SampCfg<double>::kTile;
-  const int64_t num_tiles = std::max<int64_t>(1, ceil_div(n, tile));
-  int64_t nseg = std::min<int64_t>(num_tiles, (int64_t)num_sms() * 4);
+  (void)dt;
+  // one segment per resident warp
+  const int64_t num_chunks = std::max<int64_t>(1, ceil_div(n, kChunk));
+  int64_t nseg = std::min<int64_t>(num_chunks, (int64_t)num_sms() * kSegCtasPerSm * kSegWarps);
   SegPlan pl;
-  pl.tiles_per_cta = ceil_div(num_tiles, nseg);
-  pl.nseg = ceil_div(num_tiles, pl.tiles_per_cta);
-  const double per = (double)pl.tiles_per_cta * (double)tile;
+  pl.chunks_per_seg = ceil_div(num_chunks, nseg);
+  pl.nseg = ceil_div(num_chunks, pl.chunks_per_seg);
+  const double per = (double)pl.chunks_per_seg * (double)kChunk;
   const double mean = per * q;
-  int64_t cap = (int64_t)(mean + 8.0 * std::sqrt(mean * (1.0 - q) + 1.0) + 256.0);
+  int64_t cap = (int64_t)(mean + 8.0 * std::sqrt(mean * (1.0 - q) + 1.0) + 64.0);
   if (cap > (int64_t)per || q >= 1.0) cap = (int64_t)per;
   pl.seg_cap = std::max<int64_t>(cap, 1);
   return pl;
 }
 
 mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
-                               int64_t* seg_idx, void* seg_val, int64_t* seg_count, unsigned* d_err,
-                               cudaStream_t st, bool skip) {
+                               uint32_t* seg_off, void* seg_val, int64_t* seg_count, cudaStream_t st, bool skip) {
   if (dt == MACH_F32)
-    return skip ? launch_seg_t<float, true>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st)
-                : launch_seg_t<float, false>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
-  return skip ? launch_seg_t<double, true>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st)
-              : launch_seg_t<double, false>(x, n, seed, T, pl, seg_idx, seg_val, seg_count, d_err, st);
+    return skip ? launch_seg_t<float, false>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st)
+                : launch_seg_t<float, true>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st);
+  return skip ? launch_seg_t<double, false>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st)
+              : launch_seg_t<double, true>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st);
 }
 
-mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const int64_t* seg_idx,
+mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const uint32_t* seg_off,
                               const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
                               cudaStream_t st) {
+  const int64_t span = pl.chunks_per_seg * kChunk;
   if (dt == MACH_F32)
-    seg_gather_kernel<float><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, seg_idx,
+    seg_gather_kernel<float><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, span, seg_off,
                                                                  static_cast<const float*>(seg_val), idx,
                                                                  static_cast<float*>(val), out_cap, d_err);
   else
-    seg_gather_kernel<double><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, seg_idx,
+    seg_gather_kernel<double><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, span, seg_off,
                                                                   static_cast<const double*>(seg_val), idx,
                                                                   static_cast<double*>(val), out_cap, d_err);
   MACH_LAUNCH_CHECK();
