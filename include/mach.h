@@ -212,6 +212,44 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
                       void* stream);
 
 /* ---------------------------------------------------------------------------
+ * mach_hooi_batched — Algorithm 2 for B independent 3-way samples in ONE
+ * persistent kernel launch (the loop and the core of Algorithm 2 for every
+ * sample; Section 2.1 n-mode products and "Tucker3 Algorithms").  Each CTA
+ * of the launch owns one decomposition at a time and runs all of its sweeps
+ * without returning to the host, which removes the per-mode launches that
+ * bound many small decompositions.  Unless warm_start != 0, every factor is
+ * first initialised inside the same launch by HOSVD: the r_n leading
+ * eigenvectors of X^_(n) X^_(n)^T from 8 block subspace iterations (width
+ * 16, seeded by the sample's seed) applied through the fibres along mode n,
+ * and a Rayleigh-Ritz step (the atomically accumulated products make this
+ * start reproducible to rounding only; HOOI refines it).  The sweeps are
+ * FP32: the TTM chain over the mode-n CSF, the
+ * Gram of the smaller side of Y_(n) (M = min(I_n, J_n) <= 32), its full
+ * eigendecomposition by cyclic Jacobi, A_n = Y V Lambda^-1/2 (or V), then a
+ * Cholesky re-orthonormalisation with FP64 r x r Gram, factor and inverse.
+ *
+ *   samples        host array of B sample handles, all 3-way, all with the
+ *                  same value type (MACH_F32 or MACH_F64), none empty.
+ *   ranks          host array of 3 ranks shared by every sample; every
+ *                  J_n = prod_{k != n} r_k must be <= 32.
+ *   sweeps         >= 0 (0 with warm_start == 0: the HOSVD factors).
+ *   prec           MACH_PREC_FP32 (others: MACH_EINVAL).
+ *   factors_io_dev host array of 3B device pointers, entry 3b + k = factor k
+ *                  of sample b, FP64 column-major I_k x r_k: read when
+ *                  warm_start != 0, always overwritten.  Caller-owned.
+ *   cores_dev      NULL, or host array of B device pointers (entries may be
+ *                  NULL) receiving G of sample b, r_1 r_2 r_3 FP64, C-order,
+ *                  1/p included.
+ * Asynchronous on `stream` (its staging buffers are freed stream-ordered).  Errors: MACH_EINVAL (bad
+ * handles, shapes outside the limits above, mixed value types), MACH_ENOMEM,
+ * MACH_ECUDA.  Device checks (a Gram that is not positive definite) set the
+ * status bits read by mach_sample_stats.
+ */
+mach_status mach_hooi_batched(const mach_sample_t* samples, int B, const int* ranks, int sweeps,
+                              mach_prec prec, double* const* factors_io_dev,
+                              double* const* cores_dev, int warm_start, void* stream);
+
+/* ---------------------------------------------------------------------------
  * mach_core — G = X^ x_1 A_1^T ... x_d A_d^T for given factors (Algorithm 2
  * last step, Eq. eqcore), with X^ = kept values / p.  FP64 throughout.
  *   factors_dev  d device pointers, FP64 column-major I_k x r_k (read only).

@@ -724,6 +724,36 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
                               static_cast<T*>(w.fac[n].ptr), st);
 }
 
+// HOSVD of X^: A_n = leading eigenvectors of X^_(n) X^_(n)^T, from the
+// fibres along mode n (the CSF whose leaf is n: mode (n + 1) mod d).
+template <typename T>
+mach_status hosvd_start(mach_sample_s* h, Workspace& w, const int* ranks, int sweeps, double* const* factors,
+                        cudaStream_t st) {
+  const int d = h->d;
+  for (int n = 0; n < d; ++n) {
+    const int src = (n + 1) % d;
+    const ModeCsf& M = h->mode[src];
+    const int In = (int)h->dims[n];
+    prof_begin(PROF_INITGRAM, st);
+    if (h->dt == MACH_F32)
+      MACH_TRY((launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                           static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
+                                           h->K, In, static_cast<T*>(w.C.ptr), st)));
+    else
+      MACH_TRY((launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                            static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
+                                            h->K, In, static_cast<T*>(w.C.ptr), st)));
+    // With sweeps to follow, HOOI refines the start, so the HOSVD Gram's
+    // eigenvectors are iterated at most 40 times (FP64) or 8 times (FP32,
+    // whose results are compared at 1e-5); MACH-HOSVD alone (no sweeps)
+    // iterates to convergence (at most 400).
+    const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 8) : 400;
+    MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, init_it, factors[n], st));
+    prof_end(PROF_INITGRAM, st, 0.0);
+  }
+  return MACH_OK;
+}
+
 constexpr int kBf16Refine = 3;   // FP32 refinement sweeps after the BF16 sweeps
 
 template <typename T>
@@ -737,29 +767,7 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
       MACH_TRY(launch_factor_to_rowmajor<T>(factors[k], (int)h->dims[k], ranks[k], static_cast<T*>(w.fac[k].ptr),
                                             st));
   } else {
-    // HOSVD of X^: A_n = leading eigenvectors of X^_(n) X^_(n)^T, from the
-    // fibres along mode n (the CSF whose leaf is n: mode (n + 1) mod d).
-    for (int n = 0; n < d; ++n) {
-      const int src = (n + 1) % d;
-      const ModeCsf& M = h->mode[src];
-      const int In = (int)h->dims[n];
-      prof_begin(PROF_INITGRAM, st);
-      if (h->dt == MACH_F32)
-        MACH_TRY((launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
-                                             static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
-                                             h->K, In, static_cast<T*>(w.C.ptr), st)));
-      else
-        MACH_TRY((launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
-                                              static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
-                                              h->K, In, static_cast<T*>(w.C.ptr), st)));
-      // With sweeps to follow, HOOI refines the start, so the HOSVD Gram's
-      // eigenvectors are iterated at most 40 times (FP64) or 8 times (FP32,
-      // whose results are compared at 1e-5); MACH-HOSVD alone (no sweeps)
-      // iterates to convergence (at most 400).
-      const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 8) : 400;
-      MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, init_it, factors[n], st));
-      prof_end(PROF_INITGRAM, st, 0.0);
-    }
+    MACH_TRY(hosvd_start<T>(h, w, ranks, sweeps, factors, st));
   }
   if (bf16 && sweeps > 0) {
     for (int n = 0; n < d; ++n) {
@@ -832,6 +840,103 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
       return hooi_impl<float>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st, true);
   }
   return MACH_EINVAL;
+}
+
+mach_status mach_hooi_batched(const mach_sample_t* samples, int B, const int* ranks, int sweeps, mach_prec prec,
+                              double* const* factors_io_dev, double* const* cores_dev, int warm_start, void* stream) {
+  if (B < 0 || sweeps < 0 || (B > 0 && (!samples || !ranks || !factors_io_dev))) return MACH_EINVAL;
+  if (B == 0) return MACH_OK;
+  if (prec != MACH_PREC_FP32) {
+    set_last_error("batched HOOI runs FP32 sweeps (prec must be MACH_PREC_FP32)");
+    return MACH_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const mach_dtype dt = samples[0] ? samples[0]->dt : MACH_F32;
+  int64_t ws_per = 0;
+  for (int b = 0; b < B; ++b) {
+    mach_sample_s* h = samples[b];
+    if (!h) return MACH_EINVAL;
+    if (h->d != 3) {
+      set_last_error("batched HOOI takes 3-way samples (sample %d has %d modes)", b, h->d);
+      return MACH_EINVAL;
+    }
+    if (h->dt != dt) {
+      set_last_error("batched HOOI: every sample must hold the same value type");
+      return MACH_EINVAL;
+    }
+    if (h->K == 0) {
+      set_last_error("sample %d kept no entries: nothing to decompose", b);
+      return MACH_EINVAL;
+    }
+    MACH_TRY(check_ranks(h, ranks));
+    int64_t need = 0, ymax = 0, imax = 0;
+    for (int n = 0; n < 3; ++n) {
+      imax = std::max<int64_t>(imax, h->dims[n]);
+      const int J = ranks[(n + 1) % 3] * ranks[(n + 2) % 3];
+      if (J > batched_max_j()) {
+        set_last_error("batched HOOI: mode %d has J = %d > %d (use mach_hooi)", n, J, batched_max_j());
+        return MACH_EINVAL;
+      }
+      if (!factors_io_dev[(size_t)b * 3 + n]) return MACH_EINVAL;
+      need += (h->dims[n] * ranks[n] + 31) & ~(int64_t)31;
+      ymax = std::max<int64_t>(ymax, h->dims[n] * J);
+    }
+    if (!warm_start) ymax = std::max<int64_t>(ymax, batched_hosvd_scratch(imax));
+    ws_per = std::max<int64_t>(ws_per, need + ymax);
+  }
+  // CTAs claim items in this order: largest first, so the long
+  // decompositions start at once and the short ones fill in behind them
+  std::vector<int> order((size_t)B);
+  for (int b = 0; b < B; ++b) order[(size_t)b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return samples[x]->K > samples[y]->K; });
+  std::vector<BatItem> items((size_t)B);
+  for (int o = 0; o < B; ++o) {
+    const int b = order[(size_t)o];
+    mach_sample_s* h = samples[b];
+    BatItem& it = items[(size_t)o];
+    for (int n = 0; n < 3; ++n) {
+      const ModeCsf& M = h->mode[n];
+      it.mode[n].val = M.val.ptr;
+      it.mode[n].leaf = static_cast<const uint16_t*>(M.leaf.ptr);
+      it.mode[n].fib_start = static_cast<const uint32_t*>(M.fib_start.ptr);
+      it.mode[n].fib_mid = static_cast<const uint32_t*>(M.fib_mid.ptr);
+      it.mode[n].row_fib = static_cast<const uint32_t*>(M.row_fib.ptr);
+      it.dims[n] = (int)h->dims[n];
+      it.fac[n] = factors_io_dev[(size_t)b * 3 + n];
+    }
+    it.inv_p = 1.0 / h->p;
+    it.core = cores_dev ? cores_dev[b] : nullptr;
+    it.err = &h->dscal()->err;
+    it.seed = h->seed;
+  }
+  const int grid = batched_grid(B);
+  DevBuf items_dev, ws;
+  MACH_TRY(dev_alloc(items_dev, items.size() * sizeof(BatItem) + 64, st));
+  mach_status s = dev_alloc(ws, (size_t)grid * (size_t)ws_per * sizeof(float), st);
+  if (s != MACH_OK) {
+    dev_free(items_dev, st);
+    return s;
+  }
+  BatArgs a;
+  a.items = static_cast<const BatItem*>(items_dev.ptr);
+  a.B = B;
+  for (int n = 0; n < 3; ++n) a.r[n] = ranks[n];
+  a.sweeps = sweeps;
+  a.warm = warm_start ? 1 : 0;
+  a.next = reinterpret_cast<unsigned*>(static_cast<char*>(items_dev.ptr) + items.size() * sizeof(BatItem));
+  a.ws = static_cast<float*>(ws.ptr);
+  a.ws_stride = ws_per;
+  if (cudaMemcpyAsync(items_dev.ptr, items.data(), items.size() * sizeof(BatItem), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(a.next, 0, sizeof(unsigned), st) != cudaSuccess) {
+    set_last_error("batched HOOI: %s", cudaGetErrorString(cudaGetLastError()));
+    s = MACH_ECUDA;
+  } else {
+    s = launch_batched_hooi(a, dt, grid, st);
+  }
+  dev_free(items_dev, st);
+  dev_free(ws, st);
+  return s;
 }
 
 mach_status mach_core(mach_sample_t s, const int* ranks, double* const* factors_dev, double* core_dev,

@@ -328,6 +328,38 @@ mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t
 mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const uint32_t* seg_off,
                               const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
                               cudaStream_t st);
+// Batched HOOI (batched.cu): one persistent launch over many 3-way samples.
+struct BatMode {             // the mode-n CSF of one sample
+  const void* val;           // mode-ordered values (the sample's dtype)
+  const uint16_t* leaf;      // leaf index per entry
+  const uint32_t* fib_start; // nfib + 1
+  const uint32_t* fib_mid;   // mid index per fibre
+  const uint32_t* row_fib;   // I_n + 1
+};
+struct BatItem {
+  BatMode mode[3];
+  int dims[3];
+  double inv_p;
+  double* fac[3];            // FP64 column-major I_k x r_k: start factors in, results out
+  double* core;              // r_1 r_2 r_3 FP64 (C order), or null
+  unsigned* err;             // the sample's status word
+  uint64_t seed;             // seeds the HOSVD start block
+};
+struct BatArgs {
+  const BatItem* items;
+  int B;
+  int r[3];
+  int sweeps;
+  int warm;                  // 0: HOSVD start inside the launch
+  unsigned* next;            // item counter (zero at launch)
+  float* ws;                 // grid x ws_stride floats
+  int64_t ws_stride;
+};
+int batched_max_j();
+int64_t batched_hosvd_scratch(int64_t max_dim);
+int batched_grid(int B);
+mach_status launch_batched_hooi(const BatArgs& a, mach_dtype dt, int grid, cudaStream_t st);
+
 // Fixed scratch of the allocation-free sampler (sample.cu): its size in
 // 8-byte words, the largest tensor it serves, and this device's address of it.
 constexpr int64_t kFixedScratchWords = 524288;

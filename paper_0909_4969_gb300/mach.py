@@ -46,6 +46,8 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_uint)]),
     "mach_hooi": (ctypes.c_int, [ctypes.c_void_p, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, ctypes.c_void_p,
                                  ctypes.c_int, ctypes.c_void_p]),
+    "mach_hooi_batched": (ctypes.c_int, [_c_pp, ctypes.c_int, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, _c_pp,
+                                         ctypes.c_int, ctypes.c_void_p]),
     "mach_core": (ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_pp, ctypes.c_void_p, ctypes.c_void_p]),
     "mach_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, _c_intp, _c_pp,
                                   ctypes.c_void_p, _c_dblp, _c_dblp, ctypes.c_void_p]),
@@ -225,6 +227,30 @@ class Sample:
             self.free()
         except Exception:
             pass
+
+
+def hooi_batched(samples: Sequence["Sample"], ranks: Sequence[int], sweeps: int,
+                 factors: Optional[List[List[torch.Tensor]]] = None, warm: bool = False, core: bool = True,
+                 stream=None):
+    """mach_hooi_batched: Algorithm 2 for every 3-way sample in one persistent
+    launch (FP32 sweeps).  Returns (cores or None, factors), one entry per sample."""
+    lib = load()
+    B = len(samples)
+    if factors is None:
+        if warm:
+            raise ValueError("warm start needs factors")
+        factors = [new_factors(s.dims, ranks, s.device) for s in samples]
+    else:
+        factors = [[colmajor(f) if f.stride(0) != 1 else f for f in fs] for fs in factors]
+    cores = [torch.empty(tuple(int(r) for r in ranks), dtype=torch.float64, device=s.device) for s in samples] \
+        if core else None
+    handles = (ctypes.c_void_p * max(B, 1))(*[s.handle.value for s in samples])
+    flat = [f for fs in factors for f in fs]
+    fptr = (ctypes.c_void_p * max(len(flat), 1))(*[f.data_ptr() for f in flat])
+    cptr = (ctypes.c_void_p * max(B, 1))(*[c.data_ptr() for c in cores]) if core else None
+    _check("mach_hooi_batched", lib.mach_hooi_batched(handles, B, _int(ranks), int(sweeps), PREC["fp32"], fptr,
+                                                      cptr, 1 if warm else 0, _stream(stream)))
+    return cores, factors
 
 
 def sample(x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False) -> Sample:
