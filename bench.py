@@ -419,6 +419,10 @@ def main():
     spec_r = synth.TuckerSpec(spec.dims, spec.ranks, spec.core, spec.noise, spec.seed + rank, spec.dtype)
     X, _, _ = synth.tucker_torch(spec_r, device="cuda")
     torch.cuda.synchronize()
+    # decompositions run on a stream of their own (the library replays the
+    # repeated HOOI sweeps as a captured CUDA graph, which the legacy default
+    # stream does not allow)
+    torch.cuda.set_stream(torch.cuda.Stream())
     ranks = spec.ranks
     N = X.numel()
     flush = None

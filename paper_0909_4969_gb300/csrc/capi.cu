@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 namespace mach {
@@ -70,21 +72,65 @@ static cudaEvent_t prof_event() {
   return e;
 }
 
+// While a stream is being captured, the record must become an event-record
+// node of the graph (re-armed with fresh events for every replay).
+static void prof_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 void prof_begin(int kind, cudaStream_t s) {
   std::lock_guard<std::mutex> g(g_prof_mu);
   if (!g_prof_on) return;
   g_open[kind] = prof_event();
-  cudaEventRecord(g_open[kind], s);
+  prof_record(g_open[kind], s);
 }
 
 void prof_end(int kind, cudaStream_t s, double bytes) {
   std::lock_guard<std::mutex> g(g_prof_mu);
   if (!g_prof_on || !g_open[kind]) return;
   cudaEvent_t e = prof_event();
-  cudaEventRecord(e, s);
+  prof_record(e, s);
   g_prof.push_back(ProfRec{g_open[kind], e, kind, bytes});
   g_open[kind] = nullptr;
 }
+
+// Helpers for replayed CUDA graphs: the records made while a sweep was
+// captured are taken out (that sweep never ran) and every replay pushes its
+// own records with fresh events.
+static size_t prof_mark() {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  return g_prof.size();
+}
+
+static std::vector<ProfRec> prof_take_since(size_t i) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  std::vector<ProfRec> out;
+  if (i < g_prof.size()) {
+    out.assign(g_prof.begin() + (std::ptrdiff_t)i, g_prof.end());
+    g_prof.resize(i);
+  }
+  return out;
+}
+
+static bool prof_replay_push(cudaEvent_t* a, cudaEvent_t* b, int kind, double bytes) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (!g_prof_on) return false;
+  *a = prof_event();
+  *b = prof_event();
+  g_prof.push_back(ProfRec{*a, *b, kind, bytes});
+  return true;
+}
+
+static void prof_release(cudaEvent_t e) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof_pool.push_back(e);
+}
+
+static void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void prof_patch_last_bytes(int kind, double bytes) {
   std::lock_guard<std::mutex> g(g_prof_mu);
@@ -754,6 +800,87 @@ mach_status hosvd_start(mach_sample_s* h, Workspace& w, const int* ranks, int sw
   return MACH_OK;
 }
 
+// Runs `count` more sweeps by capturing one (`body`) into a CUDA graph and
+// replaying it: sweeps after the first issue the same launches with the same
+// arguments, so the replays remove the launch gaps between the ~10 stream
+// operations of every mode update.  *done counts the sweeps run.  When the
+// capture or instantiation fails nothing has run, and the caller runs the
+// remaining sweeps directly.
+template <typename F>
+mach_status replay_sweeps(cudaStream_t st, int count, F body, int* done) {
+  if (count < 4) return MACH_OK;   // too few replays to repay the capture
+  const size_t mark = prof_mark();
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return MACH_OK;
+  }
+  const long long l0 = (long long)mach_launch_count();
+  const mach_status sb = body();
+  const long long nlaunch = (long long)mach_launch_count() - l0;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st, &g);
+  add_launches(-nlaunch);   // counted while capturing; they run in the replays
+  std::vector<ProfRec> recs = prof_take_since(mark);
+  cudaGraphExec_t ge = nullptr;
+  const bool ok = sb == MACH_OK && ec == cudaSuccess && g != nullptr &&
+                  cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  // event-record nodes of the profiling scopes, matched to their records
+  std::vector<std::pair<cudaGraphNode_t, cudaGraphNode_t>> pnodes;
+  bool profile_ok = ok;
+  if (ok && !recs.empty()) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    std::map<cudaEvent_t, cudaGraphNode_t> ev2node;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      cudaEvent_t e = nullptr;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeEventRecord &&
+          cudaGraphEventRecordNodeGetEvent(nd, &e) == cudaSuccess)
+        ev2node[e] = nd;
+    }
+    for (const ProfRec& r : recs) {
+      auto ia = ev2node.find(r.a), ib = ev2node.find(r.b);
+      if (ia == ev2node.end() || ib == ev2node.end()) {
+        profile_ok = false;
+        break;
+      }
+      pnodes.emplace_back(ia->second, ib->second);
+    }
+  }
+  for (const ProfRec& r : recs) {
+    prof_release(r.a);
+    prof_release(r.b);
+  }
+  if (!ok) {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return MACH_OK;
+  }
+  mach_status s = MACH_OK;
+  for (int k = 0; k < count; ++k) {
+    if (profile_ok)
+      for (size_t i = 0; i < pnodes.size(); ++i) {
+        cudaEvent_t a, b;
+        if (!prof_replay_push(&a, &b, recs[i].kind, recs[i].bytes)) break;
+        cudaGraphExecEventRecordNodeSetEvent(ge, pnodes[i].first, a);
+        cudaGraphExecEventRecordNodeSetEvent(ge, pnodes[i].second, b);
+      }
+    if (cudaGraphLaunch(ge, st) != cudaSuccess) {
+      set_last_error("sweep graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+      s = MACH_ECUDA;
+      break;
+    }
+    add_launches(nlaunch);
+    ++*done;
+  }
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  return s;
+}
+
 constexpr int kBf16Refine = 3;   // FP32 refinement sweeps after the BF16 sweeps
 
 template <typename T>
@@ -783,8 +910,7 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
   // iteration from the BF16 solution; each sweep contracts the BF16 error
   // by the HOOI convergence factor)
   const int total = bf16 && sweeps > 0 ? sweeps + kBf16Refine : sweeps;
-  for (int sweep = 0; sweep < total; ++sweep) {
-    const bool low = bf16 && sweep < sweeps;
+  auto one_sweep = [&](bool low) -> mach_status {
     for (int n = 0; n < d; ++n) {
       int J = 1;
       for (int k = 0; k < d; ++k)
@@ -804,7 +930,17 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
       MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, J, jroute, true, 100, factors[n], st));
       prof_end(PROF_LSV, st, 0.0);
     }
+    return MACH_OK;
+  };
+  int sweep = 0;
+  if (!bf16 && total >= 5) {
+    // the first sweep settles the warm-start state of every mode; the rest
+    // repeat its launches exactly and run as replays of one captured sweep
+    MACH_TRY(one_sweep(false));
+    sweep = 1;
+    MACH_TRY(replay_sweeps(st, total - 1, [&]() { return one_sweep(false); }, &sweep));
   }
+  for (; sweep < total; ++sweep) MACH_TRY(one_sweep(bf16 && sweep < sweeps));
   if (core) {
     const int n = d - 1;
     int J = 1;

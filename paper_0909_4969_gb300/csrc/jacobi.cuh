@@ -1,6 +1,6 @@
-// Register-resident cyclic Jacobi eigensolver for a small symmetric matrix
-// on one warp (shared by the single-CTA eigensolver and the batched HOOI
-// kernel).
+// Small dense eigensolvers shared by the single-CTA eigensolver and the
+// batched HOOI kernel: the register-resident cyclic Jacobi of one warp, and
+// the FP64 iterative refinement of a few Ritz pairs (CTAs of 256 threads).
 #pragma once
 
 #include "mach_internal.cuh"
@@ -116,6 +116,145 @@ __device__ __noinline__ void jacobi_reg(T* Hs, T* Qs, int ldm, int n, T rel_tol,
       }
   }
   __syncwarp();
+}
+
+// FP64, n <= 16, leading dimension ldm (fallback of the final Rayleigh-Ritz).
+__device__ void jacobi_warp_small(double* H, double* Qm, int ldm, int n, double rel_tol, int max_sweeps) {
+  if (n <= 8) jacobi_reg<double, 8>(H, Qm, ldm, n, rel_tol, max_sweeps);
+  else if (n <= 12) jacobi_reg<double, 12>(H, Qm, ldm, n, rel_tol, max_sweeps);
+  else jacobi_reg<double, 16>(H, Qm, ldm, n, rel_tol, max_sweeps);
+}
+
+constexpr int kRRWarps = 8;   // warps of the CTAs that call rr_refine (256 threads)
+// ----------------------------------------------------------------------------
+// Final Rayleigh-Ritz of the leading r Ritz vectors in FP64 (r <= 16).
+// Given the projected matrix H = U_r^T C U_r and the Gram G = U_r^T U_r of
+// the Ritz basis (orthonormal and diagonalising up to the b-space
+// arithmetic), the eigenvectors of the pencil (H, G) are refined with the
+// iterative refinement of Ogita and Aishima (Japan J. Indust. Appl. Math.
+// 35, 2018): for the estimate X, S = X^T H X, R = I - X^T G X,
+// lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j R_ij) /
+// (lambda_j - lambda_i) for pairs separated by more than
+// delta = 2 (||offdiag S||_F + max|lambda| ||R||_F), R_ij / 2 otherwise,
+// and X <- X (I + E).  The error is squared by every round, so from a
+// start that is diagonal to FP32 precision two rounds reach FP64
+// precision; when four rounds do not converge, a cyclic FP64 Jacobi on H
+// is used instead.  All threads of the CTA; one thread per entry.
+// ----------------------------------------------------------------------------
+constexpr int kRl = kMaxRank + 1;
+struct FinalRR {
+  double H[kMaxRank * kRl], G[kMaxRank * kRl], X[kMaxRank * kRl];
+  double T1[kMaxRank * kRl], T2[kMaxRank * kRl];
+  double lam[kMaxRank];
+  double red[3][kRRWarps];
+  double delta, emax;
+  int perm[kMaxRank];
+};
+
+__device__ void rr_refine(FinalRR& f, int r) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const bool act = tid < r * r;
+  const int i = act ? tid / r : 0, j = act ? tid - (tid / r) * r : 0;
+  if (act) f.X[i * kRl + j] = i == j ? 1.0 : 0.0;
+  __syncthreads();
+  bool ok = false;
+  for (int round = 0; round < 4 && !ok; ++round) {
+    if (act) {
+      double a = 0.0, g = 0.0;
+      for (int k = 0; k < r; ++k) {
+        const double x = f.X[k * kRl + j];
+        a += f.H[i * kRl + k] * x;
+        g += f.G[i * kRl + k] * x;
+      }
+      f.T1[i * kRl + j] = a;   // H X
+      f.T2[i * kRl + j] = g;   // G X
+    }
+    __syncthreads();
+    double sx = 0.0, rx = 0.0;
+    if (act) {
+      for (int k = 0; k < r; ++k) {
+        const double x = f.X[k * kRl + i];
+        sx += x * f.T1[k * kRl + j];
+        rx += x * f.T2[k * kRl + j];
+      }
+      rx = (i == j ? 1.0 : 0.0) - rx;
+    }
+    __syncthreads();
+    if (act) {
+      f.T1[i * kRl + j] = sx;  // S
+      f.T2[i * kRl + j] = rx;  // R
+      if (i == j) f.lam[i] = sx / (1.0 - rx);
+    }
+    double o = (act && i != j) ? sx * sx : 0.0, q = act ? rx * rx : 0.0;
+    o = warp_sum(o);
+    q = warp_sum(q);
+    if (lane == 0) {
+      f.red[0][warp] = o;
+      f.red[1][warp] = q;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double so = 0.0, sr = 0.0, lm = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        so += f.red[0][w];
+        sr += f.red[1][w];
+      }
+      for (int k = 0; k < r; ++k) lm = fmax(lm, fabs(f.lam[k]));
+      f.delta = 2.0 * (sqrt(so) + lm * sqrt(sr));
+    }
+    __syncthreads();
+    double e = 0.0;
+    if (act) {
+      if (i == j) {
+        e = 0.5 * rx;
+      } else {
+        const double li = f.lam[i], lj = f.lam[j];
+        e = fabs(lj - li) > f.delta ? (sx + lj * rx) / (lj - li) : 0.5 * rx;
+      }
+    }
+    double em = act ? fabs(e) : 0.0;
+    if (em != em) em = 1e300;   // NaN: never converged
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) em = fmax(em, __shfl_xor_sync(0xffffffffu, em, d));
+    if (lane == 0) f.red[2][warp] = em;
+    __syncthreads();
+    if (act) f.T1[i * kRl + j] = e;   // E (S no longer needed)
+    if (tid == 0) {
+      double m = 0.0;
+      for (int w = 0; w < nw; ++w) m = fmax(m, f.red[2][w]);
+      f.emax = m;
+    }
+    __syncthreads();
+    double xn = 0.0;
+    if (act) {
+      xn = f.X[i * kRl + j];
+      for (int k = 0; k < r; ++k) xn += f.X[i * kRl + k] * f.T1[k * kRl + j];
+    }
+    __syncthreads();
+    if (act) f.X[i * kRl + j] = xn;
+    // the correction of this round was below 1e-9: the remaining error is
+    // of its square
+    ok = f.emax < 1e-9;
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid < 32) {
+      jacobi_warp_small(f.H, f.X, kRl, r, 1e-15, 12);
+      if (tid < r) f.lam[tid] = f.H[tid * kRl + tid];
+    }
+    __syncthreads();
+  }
+  // descending order of lambda (ties: lower index first)
+  if (tid < r) {
+    const double v = f.lam[tid];
+    int rank = 0;
+    for (int k = 0; k < r; ++k) {
+      const double u = f.lam[k];
+      rank += (u > v) || (u == v && k < tid);
+    }
+    f.perm[rank] = tid;
+  }
+  __syncthreads();
 }
 
 }  // namespace

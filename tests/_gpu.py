@@ -43,18 +43,37 @@ def sign_fixed_core(G, factors):
     return G
 
 
-def compare_decomposition(O, X, G_o, A_o, G_g, A_g, tol, label=""):
+def min_core_gap(G):
+    """Smallest relative gap (s_j - s_{j+1}) / s_1 between consecutive
+    singular values of the core unfoldings G_(k): the singular vectors inside
+    each factor are determined only up to rotations of about rounding / gap."""
+    G = np.asarray(G, dtype=np.float64)
+    gaps = []
+    for k in range(G.ndim):
+        sv = np.linalg.svd(np.moveaxis(G, k, 0).reshape(G.shape[k], -1), compute_uv=False)
+        if sv.size > 1 and sv[0] > 0:
+            gaps.append(float(np.min(sv[:-1] - sv[1:]) / sv[0]))
+    return min(gaps) if gaps else 1.0
+
+
+def compare_decomposition(O, X, G_o, A_o, G_g, A_g, tol, label="", rounding=None):
     """Subspace distance per mode, core (after sign fix) and reconstruction
-    error of the GPU decomposition against the oracle's, all within tol."""
+    error of the GPU decomposition against the oracle's, all within tol.
+    With `rounding` (the unit roundoff of the path's arithmetic), the core is
+    compared only when every core singular-value gap g satisfies
+    rounding / g <= tol: below that, the individual singular vectors are not
+    determined to tol by that arithmetic (degenerate singular values), and the
+    subspaces and the reconstruction error carry the comparison."""
     for k in range(len(A_o)):
         dist = O.subspace_distance(A_o[k], A_g[k])
         assert dist <= tol, "%s mode %d subspace distance %.3e > %.1e" % (label, k, dist, tol)
         ortho = np.max(np.abs(A_g[k].T @ A_g[k] - np.eye(A_g[k].shape[1])))
         assert ortho <= max(tol, 1e-12), "%s mode %d not orthonormal: %.3e" % (label, k, ortho)
-    Go = sign_fixed_core(G_o, A_o)
-    Gg = sign_fixed_core(G_g, A_g)
-    rel = np.linalg.norm(Go - Gg) / np.linalg.norm(Go)
-    assert rel <= tol, "%s core relative difference %.3e > %.1e" % (label, rel, tol)
+    if rounding is None or rounding / max(min_core_gap(G_o), 1e-300) <= tol:
+        Go = sign_fixed_core(G_o, A_o)
+        Gg = sign_fixed_core(G_g, A_g)
+        rel = np.linalg.norm(Go - Gg) / np.linalg.norm(Go)
+        assert rel <= tol, "%s core relative difference %.3e > %.1e" % (label, rel, tol)
     eo = O.relative_error(X, G_o, A_o)
     eg = O.relative_error(X, G_g, A_g)
     assert abs(eo - eg) <= tol * max(1.0, eo), "%s reconstruction error %.12f vs %.12f" % (label, eg, eo)
