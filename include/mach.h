@@ -219,7 +219,7 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
  * without returning to the host, which removes the per-mode launches that
  * bound many small decompositions.  Unless warm_start != 0, every factor is
  * first initialised inside the same launch by HOSVD: the r_n leading
- * eigenvectors of X^_(n) X^_(n)^T from 8 block subspace iterations (width
+ * eigenvectors of X^_(n) X^_(n)^T from 12 block subspace iterations (width
  * 16, seeded by the sample's seed) applied through the fibres along mode n,
  * and a Rayleigh-Ritz step (the atomically accumulated products make this
  * start reproducible to rounding only; HOOI refines it).  The sweeps are

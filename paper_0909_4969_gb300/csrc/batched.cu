@@ -272,7 +272,7 @@ __device__ void bat_lsv(const float* Y, int I, int J, int r, float* A, BatShared
 }
 
 constexpr int kHosvdB = 16;     // block width of the HOSVD subspace iteration
-constexpr int kHosvdIt = 8;     // its iteration count (HOOI refines the start)
+constexpr int kHosvdIt = 12;    // its iteration count (HOOI refines the start)
 
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
