@@ -107,6 +107,31 @@ mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_
                         double p, uint64_t seed, void* stream, mach_sample_t* out);
 
 /* ---------------------------------------------------------------------------
+ * mach_sample_host — mach_sample for an input that stays in HOST memory, the
+ * setting the paper motivates MACH with (a tensor too large to hold in
+ * memory, Section 1; the exact decomposition running out of memory in
+ * Section 4): X is streamed chunk by chunk into a ring of two device
+ * buffers of chunk_entries entries, each copy (on a stream of the library's
+ * own) overlapping the coin of the previous chunk; only the kept entries
+ * and their orderings stay on the device.  The coin of entry l is the same
+ * as mach_sample's (keyed on the global l), so the kept set, values,
+ * orderings and every later result are identical to mach_sample on the same
+ * data.
+ *
+ *   x_host         host pointer to the dense C-order tensor (16-byte
+ *                  aligned; page-locked memory lets the copies overlap the
+ *                  sampler, pageable memory works but serialises them).
+ *   chunk_entries  entries per streamed chunk: 0 = 2^28, else a positive
+ *                  multiple of 2048.  The ring holds 2 chunks of device
+ *                  memory.
+ *   other arguments and errors as mach_sample (MACH_EINVAL also for a bad
+ *   chunk_entries).  Synchronises `stream`.
+ */
+mach_status mach_sample_host(const void* x_host, mach_dtype dtype, int d, const int64_t* dims,
+                             double p, uint64_t seed, int64_t chunk_entries, void* stream,
+                             mach_sample_t* out);
+
+/* ---------------------------------------------------------------------------
  * mach_sample_skip — mach_sample for an input resident in device memory,
  * reading only what the coin keeps.  The coin depends on the index alone
  * (Section 3 Remark 1), so the kept entries are known before X is read:

@@ -361,8 +361,15 @@ mach_status mach_profile_query(int kind, double* total_ms, int64_t* launches, do
 
 int64_t mach_launch_count(void) { return (int64_t)g_launches.load(); }
 
+// The input streamed from host memory: chunk_entries > 0 entries of x_host
+// at a time, copied into a ring of two device buffers on a copy stream while
+// the sampler runs on the previous chunk.
+struct HostStream {
+  int64_t chunk_entries = 0;   // 0: x is a device pointer
+};
+
 static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p, uint64_t seed,
-                               void* stream, mach_sample_t* out, bool skip) {
+                               void* stream, mach_sample_t* out, bool skip, HostStream hst = HostStream()) {
   if (!x_dev || !dims || !out) return MACH_EINVAL;
   if (d < 2 || d > kMaxModes) return MACH_EINVAL;
   if (dtype != MACH_F32 && dtype != MACH_F64) return MACH_EINVAL;
@@ -402,37 +409,91 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
   // coin + compaction: per-warp segments, then an ordered gather into idx / val
   // (sized for the segments' capacity, so no host round trip in between)
   const double q = h->T >= (1ull << 32) ? 1.0 : (double)h->T / 4294967296.0;
-  SegPlan pl = plan_segments(N, dtype, q);
+  const bool from_host = hst.chunk_entries > 0;
+  const int64_t CE = from_host ? std::min<int64_t>(hst.chunk_entries, N) : N;   // entries per input chunk
+  const int64_t nchunks = from_host ? ceil_div(N, CE) : 1;
+  SegPlan pl = plan_segments(CE, dtype, q);
   const size_t vs = dtype_size(dtype);
+  DevBuf ring[2];
+  cudaStream_t cst = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  auto release_stream = [&]() {
+    for (int b = 0; b < 2; ++b) {
+      if (copied[b]) cudaEventDestroy(copied[b]);
+      if (consumed[b]) cudaEventDestroy(consumed[b]);
+      copied[b] = consumed[b] = nullptr;
+    }
+    if (cst) cudaStreamDestroy(cst);
+    cst = nullptr;
+  };
+  if (from_host) {
+    for (int b = 0; b < 2 && b < nchunks; ++b)
+      if ((s = dev_alloc(ring[b], (size_t)CE * vs, st)) != MACH_OK) return fail(s);
+    if (cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&copied[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&copied[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&consumed[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&consumed[1], cudaEventDisableTiming) != cudaSuccess) {
+      release_stream();
+      set_last_error("host-streamed sampler: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(MACH_ECUDA);
+    }
+    // the ring buffers come from stream-ordered allocations on st
+    if (cudaEventRecord(consumed[0], st) != cudaSuccess || cudaEventRecord(consumed[1], st) != cudaSuccess) {
+      release_stream();
+      return fail(MACH_ECUDA);
+    }
+  }
   for (int attempt = 0; attempt < 2; ++attempt) {
     DevBuf seg_off, seg_val, seg_cnt;
-    const int64_t cap_all = pl.nseg * pl.seg_cap;
-    if ((s = dev_alloc(h->idx, (size_t)cap_all * 8, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(h->val, (size_t)cap_all * vs, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(seg_off, (size_t)cap_all * 4, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(seg_val, (size_t)cap_all * vs, st)) != MACH_OK) return fail(s);
-    if ((s = dev_alloc(seg_cnt, (size_t)pl.nseg * 8, st)) != MACH_OK) return fail(s);
+    const int64_t nseg_all = pl.nseg * nchunks;
+    const int64_t cap_all = nseg_all * pl.seg_cap;
+    if ((s = dev_alloc(h->idx, (size_t)cap_all * 8, st)) != MACH_OK) return release_stream(), fail(s);
+    if ((s = dev_alloc(h->val, (size_t)cap_all * vs, st)) != MACH_OK) return release_stream(), fail(s);
+    if ((s = dev_alloc(seg_off, (size_t)cap_all * 4, st)) != MACH_OK) return release_stream(), fail(s);
+    if ((s = dev_alloc(seg_val, (size_t)cap_all * vs, st)) != MACH_OK) return release_stream(), fail(s);
+    if ((s = dev_alloc(seg_cnt, (size_t)nseg_all * 8, st)) != MACH_OK) return release_stream(), fail(s);
     prof_begin(PROF_SAMPLER, st);
-    if ((s = launch_sampler_seg(x_dev, dtype, N, seed, h->T, pl, static_cast<uint32_t*>(seg_off.ptr), seg_val.ptr,
-                                static_cast<int64_t*>(seg_cnt.ptr), st, skip)) != MACH_OK)
-      return fail(s);
-    if ((s = launch_seg_gather(dtype, pl, static_cast<const int64_t*>(seg_cnt.ptr),
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int64_t l0 = c * CE, n = std::min<int64_t>(CE, N - l0);
+      const void* xc = x_dev;
+      if (from_host) {
+        const int b = (int)(c & 1);
+        // copy chunk c once the sampler has finished with the chunk two back
+        if (cudaStreamWaitEvent(cst, consumed[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(ring[b].ptr, static_cast<const char*>(x_dev) + (size_t)l0 * vs, (size_t)n * vs,
+                            cudaMemcpyHostToDevice, cst) != cudaSuccess ||
+            cudaEventRecord(copied[b], cst) != cudaSuccess || cudaStreamWaitEvent(st, copied[b], 0) != cudaSuccess) {
+          set_last_error("host-streamed sampler: %s", cudaGetErrorString(cudaGetLastError()));
+          release_stream();
+          return fail(MACH_ECUDA);
+        }
+        xc = ring[b].ptr;
+      }
+      const size_t so = (size_t)c * pl.nseg * pl.seg_cap;
+      if ((s = launch_sampler_seg(xc, dtype, n, l0, seed, h->T, pl, static_cast<uint32_t*>(seg_off.ptr) + so,
+                                  static_cast<char*>(seg_val.ptr) + so * vs,
+                                  static_cast<int64_t*>(seg_cnt.ptr) + c * pl.nseg, st, skip)) != MACH_OK)
+        return release_stream(), fail(s);
+      if (from_host && cudaEventRecord(consumed[c & 1], st) != cudaSuccess) return release_stream(), fail(MACH_ECUDA);
+    }
+    if ((s = launch_seg_gather(dtype, pl, nseg_all, CE, static_cast<const int64_t*>(seg_cnt.ptr),
                                static_cast<const uint32_t*>(seg_off.ptr), seg_val.ptr,
                                static_cast<int64_t*>(h->idx.ptr), h->val.ptr, cap_all, &ds->err, st)) != MACH_OK)
-      return fail(s);
+      return release_stream(), fail(s);
     prof_end(PROF_SAMPLER, st, 0.0);
-    std::vector<int64_t> cnt((size_t)pl.nseg);
+    std::vector<int64_t> cnt((size_t)nseg_all);
     SampleScalars hs;
     if (cudaMemcpyAsync(cnt.data(), seg_cnt.ptr, cnt.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(&hs, ds, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       set_last_error("sampler: %s", cudaGetErrorString(cudaGetLastError()));
-      return fail(MACH_ECUDA);
+      return release_stream(), fail(MACH_ECUDA);
     }
     dev_free(seg_off, st);
     dev_free(seg_val, st);
     dev_free(seg_cnt, st);
-    if (hs.err & DEV_TIMEOUT) return fail(MACH_ETIMEOUT);
+    if (hs.err & DEV_TIMEOUT) return release_stream(), fail(MACH_ETIMEOUT);
     int64_t K = 0, mx = 0;
     for (int64_t c : cnt) {
       K += c;
@@ -447,6 +508,9 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
     cudaMemsetAsync(&ds->err, 0, sizeof(unsigned), st);
     pl.seg_cap = std::max<int64_t>(mx, 1);
   }
+  // the ring is idle once the stream has synchronised above
+  release_stream();
+  for (int b = 0; b < 2; ++b) dev_free(ring[b], st);
   if (cudaMemcpyAsync(&ds->count, &h->K, sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(MACH_ECUDA);
@@ -541,6 +605,19 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
 mach_status mach_sample(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p, uint64_t seed,
                         void* stream, mach_sample_t* out) {
   return sample_impl(x_dev, dtype, d, dims, p, seed, stream, out, false);
+}
+
+mach_status mach_sample_host(const void* x_host, mach_dtype dtype, int d, const int64_t* dims, double p,
+                             uint64_t seed, int64_t chunk_entries, void* stream, mach_sample_t* out) {
+  const int64_t align = sampler_chunk_align();
+  if (chunk_entries == 0) chunk_entries = (int64_t)1 << 28;
+  if (chunk_entries < 0 || chunk_entries % align != 0) {
+    set_last_error("chunk_entries must be a positive multiple of %lld", (long long)align);
+    return MACH_EINVAL;
+  }
+  HostStream hst;
+  hst.chunk_entries = chunk_entries;
+  return sample_impl(x_host, dtype, d, dims, p, seed, stream, out, false, hst);
 }
 
 mach_status mach_sample_skip(const void* x_dev, mach_dtype dtype, int d, const int64_t* dims, double p,

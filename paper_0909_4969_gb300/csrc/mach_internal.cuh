@@ -323,11 +323,17 @@ struct SegPlan {
   int64_t seg_cap = 0;
 };
 SegPlan plan_segments(int64_t n, mach_dtype dt, double q);
-mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
-                               uint32_t* seg_off, void* seg_val, int64_t* seg_count, cudaStream_t st, bool skip);
-mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const uint32_t* seg_off,
-                              const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
-                              cudaStream_t st);
+// l0: linear index of x[0] (a multiple of sampler_chunk_align()), for a
+// tensor sampled chunk by chunk.
+mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, int64_t l0, uint64_t seed, uint64_t T,
+                               const SegPlan& pl, uint32_t* seg_off, void* seg_val, int64_t* seg_count,
+                               cudaStream_t st, bool skip);
+// Gathers nseg_total segments: segment c belongs to input chunk c / pl.nseg,
+// whose first linear index is (c / pl.nseg) * chunk_entries.
+mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, int64_t nseg_total, int64_t chunk_entries,
+                              const int64_t* seg_count, const uint32_t* seg_off, const void* seg_val, int64_t* idx,
+                              void* val, int64_t out_cap, unsigned* d_err, cudaStream_t st);
+int64_t sampler_chunk_align();
 // Batched HOOI (batched.cu): one persistent launch over many 3-way samples.
 struct BatMode {             // the mode-n CSF of one sample
   const void* val;           // mode-ordered values (the sample's dtype)

@@ -369,6 +369,7 @@ constexpr int kPrefetchAhead = 1;                        // chunks in flight per
 struct SegArgs {
   const void* x;
   int64_t n;
+  int64_t l0;           // linear index of x[0] (a multiple of kChunk): the coin is keyed on l0 + e
   PhiloxSched ks;
   uint32_t t32;
   int keep_all;
@@ -426,9 +427,9 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm) sample_seg_kernel(
   for (int64_t c = c0; c < c1; ++c) {
     if (STREAM && lane == 0 && c + kPrefetchAhead < c1) prefetch(c + kPrefetchAhead);
     const int64_t e_lane = c * kChunk + (int64_t)lane * kEntriesPerLane;
-    // q0 = e_lane / 4 is a multiple of 16, so the lane's 16 counters differ
-    // in the low word only
-    const uint64_t q0 = (uint64_t)e_lane >> 2;
+    // q0 = (l0 + e_lane) / 4 is a multiple of 16, so the lane's 16 counters
+    // differ in the low word only
+    const uint64_t q0 = (uint64_t)(a.l0 + e_lane) >> 2;
     const uint32_t q_lo = (uint32_t)q0, q_hi = (uint32_t)(q0 >> 32);
     uint64_t mask;
     if (a.keep_all) {
@@ -471,7 +472,8 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm) sample_seg_kernel(
 // (the host then reruns with the exact capacity).
 template <typename V>
 __global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restrict__ seg_count, int64_t seg_cap,
-                                                         int64_t seg_span, const uint32_t* __restrict__ seg_off,
+                                                         int64_t seg_span, int64_t nseg_chunk, int64_t chunk_entries,
+                                                         const uint32_t* __restrict__ seg_off,
                                                          const V* __restrict__ seg_val, int64_t* __restrict__ idx,
                                                          V* __restrict__ val, int64_t out_cap, unsigned* err) {
   __shared__ int64_t off;
@@ -492,7 +494,8 @@ __global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restri
     if (threadIdx.x == 0) atomicOr(err, DEV_OVERFLOW);
     return;
   }
-  const int64_t l0 = (int64_t)c * seg_span;
+  // segment c is segment c % nseg_chunk of input chunk c / nseg_chunk
+  const int64_t l0 = (int64_t)(c / nseg_chunk) * chunk_entries + (int64_t)(c % nseg_chunk) * seg_span;
   const uint32_t* so = seg_off + (size_t)c * seg_cap;
   const V* sv = seg_val + (size_t)c * seg_cap;
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -502,11 +505,12 @@ __global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restri
 }
 
 template <typename V, bool STREAM>
-mach_status launch_seg_t(const void* x, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl, uint32_t* seg_off,
-                         void* seg_val, int64_t* seg_count, cudaStream_t st) {
+mach_status launch_seg_t(const void* x, int64_t n, int64_t l0, uint64_t seed, uint64_t T, const SegPlan& pl,
+                         uint32_t* seg_off, void* seg_val, int64_t* seg_count, cudaStream_t st) {
   SegArgs a;
   a.x = x;
   a.n = n;
+  a.l0 = l0;
   a.ks = make_philox_sched(seed);
   a.keep_all = T >= (1ull << 32) ? 1 : 0;
   a.t32 = a.keep_all ? 0xffffffffu : (uint32_t)T;
@@ -541,30 +545,34 @@ SegPlan plan_segments(int64_t n, mach_dtype dt, double q) {
   return pl;
 }
 
-mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, uint64_t seed, uint64_t T, const SegPlan& pl,
-                               uint32_t* seg_off, void* seg_val, int64_t* seg_count, cudaStream_t st, bool skip) {
+mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, int64_t l0, uint64_t seed, uint64_t T,
+                               const SegPlan& pl, uint32_t* seg_off, void* seg_val, int64_t* seg_count,
+                               cudaStream_t st, bool skip) {
+  if (l0 % kChunk != 0) return MACH_EINVAL;
   if (dt == MACH_F32)
-    return skip ? launch_seg_t<float, false>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st)
-                : launch_seg_t<float, true>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st);
-  return skip ? launch_seg_t<double, false>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st)
-              : launch_seg_t<double, true>(x, n, seed, T, pl, seg_off, seg_val, seg_count, st);
+    return skip ? launch_seg_t<float, false>(x, n, l0, seed, T, pl, seg_off, seg_val, seg_count, st)
+                : launch_seg_t<float, true>(x, n, l0, seed, T, pl, seg_off, seg_val, seg_count, st);
+  return skip ? launch_seg_t<double, false>(x, n, l0, seed, T, pl, seg_off, seg_val, seg_count, st)
+              : launch_seg_t<double, true>(x, n, l0, seed, T, pl, seg_off, seg_val, seg_count, st);
 }
 
-mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, const int64_t* seg_count, const uint32_t* seg_off,
-                              const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
-                              cudaStream_t st) {
+mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, int64_t nseg_total, int64_t chunk_entries,
+                              const int64_t* seg_count, const uint32_t* seg_off, const void* seg_val, int64_t* idx,
+                              void* val, int64_t out_cap, unsigned* d_err, cudaStream_t st) {
   const int64_t span = pl.chunks_per_seg * kChunk;
   if (dt == MACH_F32)
-    seg_gather_kernel<float><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, span, seg_off,
-                                                                 static_cast<const float*>(seg_val), idx,
-                                                                 static_cast<float*>(val), out_cap, d_err);
+    seg_gather_kernel<float><<<(unsigned)nseg_total, 256, 0, st>>>(
+        seg_count, pl.seg_cap, span, pl.nseg, chunk_entries, seg_off, static_cast<const float*>(seg_val), idx,
+        static_cast<float*>(val), out_cap, d_err);
   else
-    seg_gather_kernel<double><<<(unsigned)pl.nseg, 256, 0, st>>>(seg_count, pl.seg_cap, span, seg_off,
-                                                                  static_cast<const double*>(seg_val), idx,
-                                                                  static_cast<double*>(val), out_cap, d_err);
+    seg_gather_kernel<double><<<(unsigned)nseg_total, 256, 0, st>>>(
+        seg_count, pl.seg_cap, span, pl.nseg, chunk_entries, seg_off, static_cast<const double*>(seg_val), idx,
+        static_cast<double*>(val), out_cap, d_err);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
+
+int64_t sampler_chunk_align() { return kChunk; }
 
 int64_t sampler_scratch_words(int64_t n, mach_dtype dt) {
   const int64_t tile = dt == MACH_F32 ? SampCfg<float>::kTile : SampCfg<double>::kTile;

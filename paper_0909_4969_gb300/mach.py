@@ -37,6 +37,9 @@ SIGNATURES = {
                                            _c_i64p, ctypes.c_void_p]),
     "mach_sample_skip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
                                         ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mach_sample_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_i64p, ctypes.c_double,
+                                        ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
     "mach_sample_count": (ctypes.c_int, [ctypes.c_void_p, _c_i64p]),
     "mach_sample_indices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "mach_sample_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -139,10 +142,14 @@ def colmajor(A: torch.Tensor) -> torch.Tensor:
 class Sample:
     """A sampled tensor (mach_sample_t) owning its device buffers."""
 
-    def __init__(self, x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False):
-        """skip=True: mach_sample_skip (reads only the sectors holding kept entries)."""
-        if not x.is_cuda or not x.is_contiguous():
-            raise ValueError("x must be a contiguous CUDA tensor")
+    def __init__(self, x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False,
+                 chunk_entries: int = 0):
+        """skip=True: mach_sample_skip (reads only the sectors holding kept
+        entries).  A CPU tensor x is streamed from host memory by
+        mach_sample_host (chunk_entries per chunk, 0 = the default); the
+        sample then lives on the current CUDA device."""
+        if not x.is_contiguous():
+            raise ValueError("x must be contiguous")
         lib = load()
         self._lib = lib
         self.dims = tuple(int(s) for s in x.shape)
@@ -150,11 +157,19 @@ class Sample:
         self.p = float(p)
         self.seed = int(seed)
         self.dtype = x.dtype
-        self.device = x.device
         h = ctypes.c_void_p()
-        fn = lib.mach_sample_skip if skip else lib.mach_sample
-        _check("mach_sample", fn(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), self.d, _i64(self.dims), self.p,
-                                 ctypes.c_uint64(self.seed), _stream(stream), ctypes.byref(h)))
+        if x.is_cuda:
+            self.device = x.device
+            fn = lib.mach_sample_skip if skip else lib.mach_sample
+            _check("mach_sample", fn(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), self.d, _i64(self.dims),
+                                     self.p, ctypes.c_uint64(self.seed), _stream(stream), ctypes.byref(h)))
+        else:
+            if skip:
+                raise ValueError("the sector-skipping sampler reads device memory")
+            self.device = torch.device("cuda", torch.cuda.current_device())
+            _check("mach_sample_host", lib.mach_sample_host(ctypes.c_void_p(x.data_ptr()), _dtype_code(x), self.d,
+                                                            _i64(self.dims), self.p, ctypes.c_uint64(self.seed),
+                                                            int(chunk_entries), _stream(stream), ctypes.byref(h)))
         self._h = h
 
     @property
@@ -253,8 +268,8 @@ def hooi_batched(samples: Sequence["Sample"], ranks: Sequence[int], sweeps: int,
     return cores, factors
 
 
-def sample(x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False) -> Sample:
-    return Sample(x, p, seed, stream, skip)
+def sample(x: torch.Tensor, p: float, seed: int, stream=None, skip: bool = False, chunk_entries: int = 0) -> Sample:
+    return Sample(x, p, seed, stream, skip, chunk_entries)
 
 
 def sample_noalloc(x: torch.Tensor, p: float, seed: int, idx_out: torch.Tensor, val_out: torch.Tensor,
