@@ -12,7 +12,14 @@ from tests._gpu import compare_decomposition, mach_module, torch
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-U32 = 2.0 ** -24   # unit roundoff of the FP32 sweeps
+# The 1e-5 bound of the reduced-precision paths is stated for subspaces and
+# reconstruction error (both rotation-invariant), which every check below
+# compares.  The sign-fixed core additionally needs the individual singular
+# vectors: an FP32 Gram and eigensolver fix them to about
+# sqrt(I) * 2^-24 / gap, below 1e-5 at these window sizes (I <= 160) only
+# for core singular-value gaps above ~5e-2, so the core is compared there.
+CORE_GAP = 5e-2
+U32 = CORE_GAP * TOL   # compare_decomposition compares the core when U32 / gap <= TOL
 
 
 def batch_specs(n, seed0=0):
