@@ -199,18 +199,22 @@ __device__ __forceinline__ void solve_row(T (&row)[kB], const T* d, const T* R, 
 // copy with 8 independent loads in flight per thread
 template <typename T>
 __device__ void stage_rows(T* dst, int ldd, const T* __restrict__ src, int lds, int rows, int cols) {
-  const int n = rows * cols, nthr = blockDim.x;
-  for (int o0 = threadIdx.x; o0 < n; o0 += 8 * nthr) {
-    T v[8];
+  // warps take 4 rows at a time, lanes the columns: coalesced row segments,
+  // 8 independent loads per lane in flight, no index division
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 4 * warp; i0 < rows; i0 += 4 * nw) {
+    for (int j0 = 0; j0 < cols; j0 += 64) {
+      T v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int o = o0 + u * nthr;
-      v[u] = o < n ? src[(size_t)(o / cols) * lds + (o - (o / cols) * cols)] : T(0);
-    }
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + (u & 3), j = j0 + 32 * (u >> 2) + lane;
+        v[u] = (i < rows && j < cols) ? src[(size_t)i * lds + j] : T(0);
+      }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int o = o0 + u * nthr;
-      if (o < n) dst[(o / cols) * ldd + (o - (o / cols) * cols)] = v[u];
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + (u & 3), j = j0 + 32 * (u >> 2) + lane;
+        if (i < rows && j < cols) dst[i * ldd + j] = v[u];
+      }
     }
   }
 }
@@ -460,18 +464,16 @@ __device__ void apply_rows(const T* X, const T* S, int b, int ncols, T* Out, int
 // order of lambda; theta = the sorted lambda.
 template <typename T>
 __device__ void rr_write(const T* U, int ld, int M, int r, const FinalRR& f, double* Vout, double* theta) {
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    double u[kMaxRank];
+  // one thread per entry (i, j); each sum over k runs in the same order as
+  // a row-at-a-time loop
+  for (int e = threadIdx.x; e < M * r; e += blockDim.x) {
+    const int i = e / r, j = e - (e / r) * r;
+    const int pj = f.perm[j];
+    double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < kMaxRank; ++k) u[k] = k < r ? (double)U[(size_t)i * ld + k] : 0.0;
-    for (int j = 0; j < r; ++j) {
-      const int pj = f.perm[j];
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < kMaxRank; ++k)
-        if (k < r) s += u[k] * f.X[k * kRl + pj];
-      Vout[(size_t)i * r + j] = s;
-    }
+    for (int k = 0; k < kMaxRank; ++k)
+      if (k < r) s += (double)U[(size_t)i * ld + k] * f.X[k * kRl + pj];
+    Vout[(size_t)i * r + j] = s;
   }
   if (threadIdx.x < r) theta[threadIdx.x] = f.lam[f.perm[threadIdx.x]];
   __syncthreads();
