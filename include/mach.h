@@ -237,6 +237,33 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
                       void* stream);
 
 /* ---------------------------------------------------------------------------
+ * mach_hooi_tucker2 — Tucker2 of a 3-way sample: mode keep_mode stays whole,
+ * the other two are compressed (Section 2.1: compressing n of the d modes
+ * gives a Tucker-n decomposition; Section 4 applies a Tucker2 to the sensor
+ * tensor).  Algorithm 2 with the kept mode's products left out: HOSVD starts
+ * for the compressed modes (unless warm_start != 0), `sweeps` Gauss-Seidel
+ * sweeps in which A_n (n compressed) is the r_n leading left singular vectors
+ * of Y_(n), Y = X^ x_m A_m^T (m the other compressed mode, the kept mode not
+ * multiplied), then the core.
+ *
+ *   ranks        host array of 3; entries of the compressed modes in
+ *                [1, min(I_k, 16, r_other * I_keep)]; the kept mode's entry is
+ *                ignored (its rank is I_keep).
+ *   keep_mode    0, 1 or 2.
+ *   prec         MACH_PREC_FP64 or MACH_PREC_FP32.
+ *   factors_dev  3 device pointers, FP64 column-major: I_k x r_k for the
+ *                compressed modes (read when warm_start != 0, overwritten),
+ *                I_keep x I_keep for the kept mode (set to the identity).
+ *   core_dev     NULL, or r'_1 r'_2 r'_3 FP64 entries (r'_keep = I_keep),
+ *                C order, 1/p included.
+ * Errors: MACH_EINVAL (not 3-way, bad ranks or mode, empty sample),
+ * MACH_ENOMEM, MACH_ECUDA.
+ */
+mach_status mach_hooi_tucker2(mach_sample_t s, const int* ranks, int keep_mode, int sweeps,
+                              mach_prec prec, double* const* factors_dev, double* core_dev,
+                              int warm_start, void* stream);
+
+/* ---------------------------------------------------------------------------
  * mach_hooi_batched — Algorithm 2 for B independent 3-way samples in ONE
  * persistent kernel launch (the loop and the core of Algorithm 2 for every
  * sample; Section 2.1 n-mode products and "Tucker3 Algorithms").  Each CTA

@@ -308,19 +308,27 @@ def hosvd(S: SampledTensor, ranks):
     return core(S, A), A
 
 
-def hooi(S: SampledTensor, ranks, sweeps: int, init=None, history=None):
+def hooi(S: SampledTensor, ranks, sweeps: int, init=None, history=None, keep=()):
     """Algorithm 2 after the coin: HOSVD initialisation (or the given factors),
     ``sweeps`` Gauss-Seidel sweeps over i = 1..d, then the core.
 
+    ``keep``: modes left uncompressed (Section 2.1: compressing only some of
+    the modes gives a Tucker-n decomposition, e.g. the Tucker2 of Section 4);
+    their factor is the identity, never updated, and their rank is I_k.
+
     If ``history`` is a list, the norm of the core after every sweep is
     appended to it (HOOI never decreases it)."""
-    ranks = [int(r) for r in ranks]
+    keep = set(int(k) for k in keep)
+    ranks = [int(S.dims[k]) if k in keep else int(r) for k, r in enumerate(ranks)]
     if init is None:
-        A = [hosvd_factor(S, k, ranks[k]) for k in range(S.d)]
+        A = [np.eye(S.dims[k]) if k in keep else hosvd_factor(S, k, ranks[k]) for k in range(S.d)]
     else:
-        A = [np.array(a, dtype=np.float64, copy=True) for a in init]
+        A = [np.eye(S.dims[k]) if k in keep else np.array(a, dtype=np.float64, copy=True)
+             for k, a in enumerate(init)]
     for _ in range(int(sweeps)):
         for i in range(S.d):
+            if i in keep:
+                continue
             Y = ttm_chain(S, A, skip=i)
             A[i] = leading_left_singular_vectors(unfold(Y, i), ranks[i])
         if history is not None:
@@ -333,6 +341,14 @@ def mach_hooi(X: np.ndarray, ranks, p: float, seed: int, sweeps: int):
     idx, vals = sample(X, p, seed)
     S = SampledTensor(X.shape, idx, vals, p)
     G, A = hooi(S, ranks, sweeps)
+    return S, G, A
+
+
+def mach_tucker2(X: np.ndarray, ranks, keep: int, p: float, seed: int, sweeps: int):
+    """Algorithm 2 as a Tucker2: mode ``keep`` stays whole (identity factor)."""
+    idx, vals = sample(X, p, seed)
+    S = SampledTensor(X.shape, idx, vals, p)
+    G, A = hooi(S, ranks, sweeps, keep=(keep,))
     return S, G, A
 
 

@@ -810,10 +810,11 @@ mach_status run_ttmc(mach_sample_s* h, Workspace& w, const int* ranks, int n, cu
 // Leading r eigenvectors of the M x M Gram in w.C -> factor n (FP64 out + T copy).
 template <typename T>
 mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, int J, bool jroute, bool warm,
-                         int maxit, double* fac_out, cudaStream_t st) {
+                         int maxit, double* fac_out, cudaStream_t st, const T* Y = nullptr) {
   const int M = jroute ? J : I;
   const int b = block_size_for(M, r, !warm, sizeof(T) == 8);
-  MACH_TRY(launch_start_block<T>(static_cast<const T*>(w.Y.ptr), static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
+  if (!Y) Y = static_cast<const T*>(w.Y.ptr);
+  MACH_TRY(launch_start_block<T>(Y, static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
                                  jroute, warm, static_cast<T*>(w.V.ptr), static_cast<T*>(w.ytpart.ptr),
                                  0x1000u + (uint32_t)n, st));
   // Columns r..b of the start block: the previous solve's Ritz vectors of the
@@ -841,7 +842,7 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.basis_out = w.basis[n].ptr;
   e.rr = static_cast<double*>(w.gram64.ptr);
   MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));
-  return launch_lsv_finish<T>(static_cast<const T*>(w.Y.ptr), e.Vout, e.theta, I, J, r, jroute,
+  return launch_lsv_finish<T>(Y, e.Vout, e.theta, I, J, r, jroute,
                               static_cast<double*>(w.A64.ptr), static_cast<double*>(w.gram64.ptr),
                               &h->dscal()->counter, static_cast<double*>(w.rinv.ptr), &h->dscal()->err, fac_out,
                               static_cast<T*>(w.fac[n].ptr), st);
@@ -1030,6 +1031,102 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
   return MACH_OK;
 }
 
+// Tucker2 (mode c kept whole, the other two compressed), Algorithm 2 with
+// the n-mode products of the kept mode left out: HOSVD starts for the
+// compressed modes, then sweeps over them (Gauss-Seidel), then the core.
+template <typename T>
+mach_status tucker2_impl(mach_sample_s* h, const int* ranks, int c, int sweeps, double* const* factors, double* core,
+                         bool warm, cudaStream_t st) {
+  const int cm[2] = {c == 0 ? 1 : 0, c == 2 ? 1 : 2};   // the compressed modes, increasing
+  int wranks[3];
+  for (int k = 0; k < 3; ++k) wranks[k] = k == c ? 1 : ranks[k];
+  Workspace& w = h->ws[sizeof(T) == 8 ? 1 : 0];
+  MACH_TRY(ensure_ws<T>(h, wranks, w));
+  const int I_c = (int)h->dims[c];
+  int64_t ymax = 1;
+  for (int q = 0; q < 2; ++q) ymax = std::max<int64_t>(ymax, h->dims[cm[q]] * ranks[cm[1 - q]] * (int64_t)I_c);
+  DevBuf Y2;
+  MACH_TRY(dev_alloc(Y2, (size_t)ymax * sizeof(T), st));
+  T* Y = static_cast<T*>(Y2.ptr);
+  auto done = [&](mach_status s) {
+    dev_free(Y2, st);
+    return s;
+  };
+  mach_status s = launch_identity_colmajor(factors[c], I_c, st);
+  if (s != MACH_OK) return done(s);
+  if (warm) {
+    for (int q = 0; q < 2; ++q)
+      if ((s = launch_factor_to_rowmajor<T>(factors[cm[q]], (int)h->dims[cm[q]], ranks[cm[q]],
+                                            static_cast<T*>(w.fac[cm[q]].ptr), st)) != MACH_OK)
+        return done(s);
+  } else {
+    for (int q = 0; q < 2; ++q) {
+      const int n = cm[q], src = (n + 1) % 3, In = (int)h->dims[n];
+      const ModeCsf& M = h->mode[src];
+      if (h->dt == MACH_F32)
+        s = launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                       static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src], h->K,
+                                       In, static_cast<T*>(w.C.ptr), st);
+      else
+        s = launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                        static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src], h->K,
+                                        In, static_cast<T*>(w.C.ptr), st);
+      if (s != MACH_OK) return done(s);
+      const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 8) : 400;
+      if ((s = solve_factor<T>(h, w, n, ranks[n], In, In, false, false, init_it, factors[n], st)) != MACH_OK)
+        return done(s);
+    }
+  }
+  // Y_(n) for compressed mode n: the leaf level of the CSF whose leaf is the
+  // other compressed mode m
+  auto mode_y = [&](int q) -> mach_status {
+    const int n = cm[q], m = cm[1 - q], src = (m + 1) % 3;
+    const ModeCsf& M = h->mode[src];
+    Tucker2Leaf a;
+    a.val = M.val.ptr;
+    a.leaf = static_cast<const uint16_t*>(M.leaf.ptr);
+    a.fib_start = static_cast<const uint32_t*>(M.fib_start.ptr);
+    a.fib_mid = static_cast<const uint32_t*>(M.fib_mid.ptr);
+    a.row_fib = static_cast<const uint32_t*>(M.row_fib.ptr);
+    a.rows = (int)h->dims[src];
+    a.Am = w.fac[m].ptr;
+    a.rm = ranks[m];
+    a.row_is_n = src == n ? 1 : 0;
+    a.I_n = (int)h->dims[n];
+    a.I_c = I_c;
+    a.Y = Y;
+    return launch_tucker2_leaf<T>(a, h->dt, st);
+  };
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int q = 0; q < 2; ++q) {
+      const int n = cm[q], m = cm[1 - q], In = (int)h->dims[n];
+      const int J = ranks[m] * I_c;
+      if ((s = mode_y(q)) != MACH_OK) return done(s);
+      const bool jroute = J < In;
+      const int Mg = jroute ? J : In;
+      prof_begin(PROF_LSV, st);
+      if (jroute)
+        s = launch_gram<T>(Y, In, Mg, J, 1, static_cast<T*>(w.C.ptr), static_cast<T*>(w.gram_part.ptr),
+                           w.gram_part_cap, st);
+      else
+        s = launch_gram<T>(Y, J, Mg, 1, J, static_cast<T*>(w.C.ptr), static_cast<T*>(w.gram_part.ptr),
+                           w.gram_part_cap, st);
+      if (s != MACH_OK) return done(s);
+      if ((s = solve_factor<T>(h, w, n, ranks[n], In, J, jroute, true, 100, factors[n], st, Y)) != MACH_OK)
+        return done(s);
+      prof_end(PROF_LSV, st, 0.0);
+    }
+  }
+  if (core) {
+    const int L = cm[1], O = cm[0];
+    if (sweeps == 0 && (s = mode_y(1)) != MACH_OK) return done(s);
+    if ((s = launch_tucker2_core<T>(Y, factors[L], (int)h->dims[L], ranks[L], ranks[O], I_c, L, O, c, 1.0 / h->p,
+                                    core, st)) != MACH_OK)
+      return done(s);
+  }
+  return done(MACH_OK);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1052,6 +1149,41 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
     case MACH_PREC_BF16_REFINE:
       return hooi_impl<float>(s, ranks, sweeps, factors_dev, core_dev, warm_start != 0, st, true);
   }
+  return MACH_EINVAL;
+}
+
+mach_status mach_hooi_tucker2(mach_sample_t s, const int* ranks, int keep_mode, int sweeps, mach_prec prec,
+                              double* const* factors_dev, double* core_dev, int warm_start, void* stream) {
+  if (!s || !ranks || !factors_dev || sweeps < 0) return MACH_EINVAL;
+  if (s->d != 3) {
+    set_last_error("Tucker2 takes a 3-way sample");
+    return MACH_EINVAL;
+  }
+  if (keep_mode < 0 || keep_mode > 2) return MACH_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (!factors_dev[k]) return MACH_EINVAL;
+  const int c = keep_mode;
+  for (int k = 0; k < 3; ++k) {
+    if (k == c) continue;
+    const int other = 3 - c - k;
+    const int64_t J = (int64_t)ranks[other] * s->dims[c];
+    if (ranks[k] < 1 || ranks[k] > kMaxRank || ranks[k] > s->dims[k] || ranks[k] > J) {
+      set_last_error("rank %d of mode %d outside [1, min(I_k, %d, r_other * I_keep)]", ranks[k], k, kMaxRank);
+      return MACH_EINVAL;
+    }
+  }
+  if (s->K == 0) {
+    set_last_error("the sample kept no entries: nothing to decompose");
+    return MACH_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s->stream = st;
+  switch (prec) {
+    case MACH_PREC_FP64: return tucker2_impl<double>(s, ranks, c, sweeps, factors_dev, core_dev, warm_start != 0, st);
+    case MACH_PREC_FP32: return tucker2_impl<float>(s, ranks, c, sweeps, factors_dev, core_dev, warm_start != 0, st);
+    default: break;
+  }
+  set_last_error("Tucker2 runs FP64 or FP32 sweeps");
   return MACH_EINVAL;
 }
 

@@ -334,6 +334,27 @@ mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, int64_t nseg_tot
                               const int64_t* seg_count, const uint32_t* seg_off, const void* seg_val, int64_t* idx,
                               void* val, int64_t out_cap, unsigned* d_err, cudaStream_t st);
 int64_t sampler_chunk_align();
+// Tucker2 of a 3-way sample (tucker2.cu).
+struct Tucker2Leaf {
+  const void* val;             // the source CSF (leaf index = the contracted mode m)
+  const uint16_t* leaf;
+  const uint32_t* fib_start;
+  const uint32_t* fib_mid;
+  const uint32_t* row_fib;
+  int rows;                    // rows of the source CSF
+  const void* Am;              // A_m, I_m x r_m row-major (T)
+  int rm;
+  int row_is_n;                // the source CSF's row index is i_n (else it is i_c)
+  int I_n, I_c;
+  void* Y;                     // I_n x (r_m * I_c), row-major (T)
+};
+template <typename T>
+mach_status launch_tucker2_leaf(const Tucker2Leaf& a, mach_dtype vdt, cudaStream_t st);
+template <typename T>
+mach_status launch_tucker2_core(const T* Y, const double* A_L, int I_L, int r_L, int r_O, int I_c, int L, int O,
+                                int c, double scale, double* G, cudaStream_t st);
+mach_status launch_identity_colmajor(double* A, int n, cudaStream_t st);
+
 // Batched HOOI (batched.cu): one persistent launch over many 3-way samples.
 struct BatMode {             // the mode-n CSF of one sample
   const void* val;           // mode-ordered values (the sample's dtype)

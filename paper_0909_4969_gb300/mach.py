@@ -49,6 +49,8 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_uint)]),
     "mach_hooi": (ctypes.c_int, [ctypes.c_void_p, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, ctypes.c_void_p,
                                  ctypes.c_int, ctypes.c_void_p]),
+    "mach_hooi_tucker2": (ctypes.c_int, [ctypes.c_void_p, _c_intp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_pp,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "mach_hooi_batched": (ctypes.c_int, [_c_pp, ctypes.c_int, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, _c_pp,
                                          ctypes.c_int, ctypes.c_void_p]),
     "mach_core": (ctypes.c_int, [ctypes.c_void_p, _c_intp, _c_pp, ctypes.c_void_p, ctypes.c_void_p]),
@@ -215,6 +217,24 @@ class Sample:
         _check("mach_hooi", self._lib.mach_hooi(self.handle, _int(ranks), int(sweeps), PREC[prec], _ptrs(factors),
                                                 ctypes.c_void_p(G.data_ptr() if G is not None else 0),
                                                 1 if warm else 0, _stream(stream)))
+        return G, factors
+
+    def tucker2(self, ranks: Sequence[int], keep: int, sweeps: int, prec: str = "fp32",
+                factors: Optional[List[torch.Tensor]] = None, warm: bool = False, core: bool = True, stream=None):
+        """mach_hooi_tucker2: mode `keep` stays whole; returns (core or None, factors),
+        the kept mode's factor being the identity."""
+        full = [int(self.dims[k]) if k == keep else int(r) for k, r in enumerate(ranks)]
+        if factors is None:
+            if warm:
+                raise ValueError("warm start needs factors")
+            factors = new_factors(self.dims, full, self.device)
+        else:
+            factors = [colmajor(f) if f.stride(0) != 1 else f for f in factors]
+        G = torch.empty(tuple(full), dtype=torch.float64, device=self.device) if core else None
+        _check("mach_hooi_tucker2", self._lib.mach_hooi_tucker2(self.handle, _int(full), int(keep), int(sweeps),
+                                                                PREC[prec], _ptrs(factors),
+                                                                ctypes.c_void_p(G.data_ptr() if G is not None else 0),
+                                                                1 if warm else 0, _stream(stream)))
         return G, factors
 
     def core(self, ranks: Sequence[int], factors: Sequence[torch.Tensor], stream=None) -> torch.Tensor:

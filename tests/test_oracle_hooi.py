@@ -155,3 +155,45 @@ def test_synthetic_inverse_sum_loose():
     S, G, A = O.mach_hooi(X, gold["ranks"], gold["p"], 2009, 3)
     for k in range(3):
         assert abs(O.pearson(Ae[k][:, 0], A[k][:, 0])) >= 0.98
+
+
+def test_tucker2_equals_tucker3_with_full_rank_in_the_kept_mode():
+    """Tucker2 (mode c whole, Section 2.1 Tucker-n) is Tucker3 with r_c = I_c:
+    a full orthonormal A_c only rotates the kept mode, so the compressed
+    factors, the projection and the reconstruction error coincide.  The
+    Tucker3 route computes its A_c by SVD and shares no Tucker2 branch."""
+    X, _, _ = synth.tucker_numpy(synth.TuckerSpec((12, 9, 5), (3, 2, 3), "gaussian", 0.2, 4, "float64"))
+    idx, vals = O.sample(X, 0.5, 21)
+    S = O.SampledTensor(X.shape, idx, vals, 0.5)
+    G2, A2 = O.hooi(S, (3, 2, 0), 6, keep=(2,))
+    G3, A3 = O.hooi(S, (3, 2, 5), 6)
+    assert np.allclose(A2[2], np.eye(5)) and G2.shape == (3, 2, 5)
+    for k in (0, 1):
+        assert O.subspace_distance(A2[k], A3[k]) < 1e-10
+    assert abs(O.relative_error(X, G2, A2) - O.relative_error(X, G3, A3)) < 1e-12
+    assert abs(O.norm(G2) - O.norm(G3)) < 1e-12 * O.norm(G3)
+
+
+def test_tucker2_p_one_matches_brute_force_and_recovers_exact_rank():
+    """At p = 1 the oracle's Tucker2 equals an independent Kronecker-form
+    Tucker2 (identity for the kept mode), and a tensor of exact rank in the
+    compressed modes is recovered to rounding."""
+    rng = np.random.default_rng(5)
+    U0 = np.linalg.qr(rng.standard_normal((10, 3)))[0]
+    U2 = np.linalg.qr(rng.standard_normal((11, 2)))[0]
+    C = rng.standard_normal((3, 6, 2))
+    X = O.mode_product(O.mode_product(C, U0, 0), U2, 2)          # mode 1 (size 6) stays whole
+    idx, vals = O.sample(X, 1.0, 1)
+    S = O.SampledTensor(X.shape, idx, vals, 1.0)
+    G, A = O.hooi(S, (3, 0, 2), 3, keep=(1,))
+    assert O.relative_error(X, G, A) < 1e-13
+    # brute force: Kronecker-form chain with A_1 = I, dense SVDs
+    B = [O.leading_left_singular_vectors(O.unfold(X, 0), 3), np.eye(6),
+         O.leading_left_singular_vectors(O.unfold(X, 2), 2)]
+    for _ in range(3):
+        for n in (0, 2):
+            others = [k for k in range(3) if k != n]
+            K = np.kron(B[others[1]], B[others[0]])
+            B[n] = O.leading_left_singular_vectors(O.unfold(X, n) @ K, B[n].shape[1])
+    for k in (0, 2):
+        assert O.subspace_distance(A[k], B[k]) < 1e-12
