@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mach", choices=["mach", "reference"])
-    ap.add_argument("--workload", default="large_fp32", choices=["large_fp32", "plain_fp64", "mixed_4way", "served", "batched"])
+    ap.add_argument("--workload", default="large_fp32", choices=["large_fp32", "plain_fp64", "mixed_4way", "served", "batched",
+                                                       "tucker2_sensor"])
     ap.add_argument("--requests", type=int, default=400, help="served: requests in the timed run")
     ap.add_argument("--slots", type=int, default=8, help="served / batched: concurrent slots")
     ap.add_argument("--budget-gb", type=float, default=48.0, help="served / batched: HBM budget")
@@ -56,6 +57,8 @@ def workload(args):
     from paper_0909_4969_gb300 import synth
     if args.workload == "plain_fp64":
         w = synth.config_plain_fp64()
+    elif args.workload == "tucker2_sensor":
+        w = synth.config_tucker2_sensor()
     elif args.workload == "mixed_4way":
         w = synth.config_mixed_4way(200 if args.scale == 1000 else args.scale)
     else:
@@ -390,10 +393,14 @@ def run_batched(args):
 
 
 def config_dict(w, prec):
-    return {"workload": w.name, "dims": list(w.spec.dims), "ranks": list(w.spec.ranks), "p": w.p,
-            "sweeps": w.sweeps, "noise": w.spec.noise, "core": w.spec.core, "input_dtype": w.spec.dtype,
-            "prec": prec, "init": "HOSVD", "l2": "inputs larger than L2 (no flush)"
-            if math.prod(w.spec.dims) * (4 if w.spec.dtype == "float32" else 8) > 129e6 else "L2 flushed"}
+    c = {"workload": w.name, "dims": list(w.spec.dims), "ranks": list(w.spec.ranks), "p": w.p,
+         "sweeps": w.sweeps, "noise": w.spec.noise, "core": w.spec.core, "input_dtype": w.spec.dtype,
+         "prec": prec, "init": "HOSVD", "l2": "inputs larger than L2 (no flush)"
+         if math.prod(w.spec.dims) * (4 if w.spec.dtype == "float32" else 8) > 129e6 else "L2 flushed"}
+    if w.name.startswith("tucker2"):
+        c["decomposition"] = "Tucker2: ranks (%d, %d), mode 3 (time) kept whole; generator rank %s" % (
+            w.spec.ranks[0], w.spec.ranks[1], list(w.spec.ranks))
+    return c
 
 
 # ----------------------------------------------------------------------------
@@ -446,7 +453,10 @@ def main():
 
     def step(x):
         s = mach.sample(x, w.p, spec_r.seed)
-        G, A = s.hooi(ranks, w.sweeps, prec)
+        if args.workload == "tucker2_sensor":
+            G, A = s.tucker2((ranks[0], ranks[1], 0), 2, w.sweeps, prec)   # time mode kept whole
+        else:
+            G, A = s.hooi(ranks, w.sweeps, prec)
         last_stats.clear()
         last_stats.update(s.stats())
         s.free()

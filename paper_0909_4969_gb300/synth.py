@@ -150,6 +150,16 @@ def config_plain_fp64() -> Workload:
                     0.1, 10, "fp64")
 
 
+def config_tucker2_sensor() -> Workload:
+    """Sensor-shaped tensor (sensors x measurement types x timeticks, the
+    shape of the paper's sensor data): 54 x 4 x 5385 FP32, Tucker rank
+    (5, 2, 8) plus 10% noise, p = 0.1, 10 sweeps; decomposed as a Tucker2
+    with the time mode kept whole and ranks (5, 2) for the other two."""
+    return Workload("tucker2_sensor_54x4x5385",
+                    TuckerSpec((54, 4, 5385), (5, 2, 8), "gaussian", 0.10, 0, "float32"),
+                    0.1, 10, "fp32")
+
+
 def config_large_fp32(scale: int = 1000) -> Workload:
     """scale^3 FP32 (1000^3 = 4 GB at full size), core 10^3, 5% noise, p = 0.01, ranks 10, 20 sweeps."""
     return Workload("large_fp32_%dx%dx%d" % (scale, scale, scale),
