@@ -557,7 +557,7 @@ def main():
         for _ in range(args.e2e_steps):
             xdev.copy_(host, non_blocking=True)
             G, A = step(xdev)
-            outs = [G.cpu()] + [a.cpu() for a in A]
+            outs = [G.cpu()] + [a.cpu() for a in A if a is not None]
             d2h = sum(o.numel() * o.element_size() for o in outs)
         f1.record(stream)
         torch.cuda.synchronize()

@@ -252,8 +252,9 @@ mach_status mach_hooi(mach_sample_t s, const int* ranks, int sweeps, mach_prec p
  *   keep_mode    0, 1 or 2.
  *   prec         MACH_PREC_FP64 or MACH_PREC_FP32.
  *   factors_dev  3 device pointers, FP64 column-major: I_k x r_k for the
- *                compressed modes (read when warm_start != 0, overwritten),
- *                I_keep x I_keep for the kept mode (set to the identity).
+ *                compressed modes (read when warm_start != 0, overwritten);
+ *                for the kept mode NULL (nothing written) or I_keep x I_keep
+ *                (set to the identity).
  *   core_dev     NULL, or r'_1 r'_2 r'_3 FP64 entries (r'_keep = I_keep),
  *                C order, 1/p included.
  * Errors: MACH_EINVAL (not 3-way, bad ranks or mode, empty sample),

@@ -1052,8 +1052,8 @@ mach_status tucker2_impl(mach_sample_s* h, const int* ranks, int c, int sweeps, 
     dev_free(Y2, st);
     return s;
   };
-  mach_status s = launch_identity_colmajor(factors[c], I_c, st);
-  if (s != MACH_OK) return done(s);
+  mach_status s = MACH_OK;
+  if (factors[c] && (s = launch_identity_colmajor(factors[c], I_c, st)) != MACH_OK) return done(s);
   if (warm) {
     for (int q = 0; q < 2; ++q)
       if ((s = launch_factor_to_rowmajor<T>(factors[cm[q]], (int)h->dims[cm[q]], ranks[cm[q]],
@@ -1161,7 +1161,7 @@ mach_status mach_hooi_tucker2(mach_sample_t s, const int* ranks, int keep_mode, 
   }
   if (keep_mode < 0 || keep_mode > 2) return MACH_EINVAL;
   for (int k = 0; k < 3; ++k)
-    if (!factors_dev[k]) return MACH_EINVAL;
+    if (!factors_dev[k] && k != keep_mode) return MACH_EINVAL;
   const int c = keep_mode;
   for (int k = 0; k < 3; ++k) {
     if (k == c) continue;

@@ -221,18 +221,20 @@ class Sample:
 
     def tucker2(self, ranks: Sequence[int], keep: int, sweeps: int, prec: str = "fp32",
                 factors: Optional[List[torch.Tensor]] = None, warm: bool = False, core: bool = True, stream=None):
-        """mach_hooi_tucker2: mode `keep` stays whole; returns (core or None, factors),
-        the kept mode's factor being the identity."""
+        """mach_hooi_tucker2: mode `keep` stays whole; returns (core or None,
+        factors) with None in place of the kept mode's (identity) factor."""
         full = [int(self.dims[k]) if k == keep else int(r) for k, r in enumerate(ranks)]
         if factors is None:
             if warm:
                 raise ValueError("warm start needs factors")
-            factors = new_factors(self.dims, full, self.device)
+            factors = new_factors(self.dims, [1 if k == keep else r for k, r in enumerate(full)], self.device)
         else:
-            factors = [colmajor(f) if f.stride(0) != 1 else f for f in factors]
+            factors = [colmajor(f) if f is not None and f.stride(0) != 1 else f for f in factors]
+        factors = [None if k == keep else f for k, f in enumerate(factors)]
         G = torch.empty(tuple(full), dtype=torch.float64, device=self.device) if core else None
+        fptr = (ctypes.c_void_p * len(factors))(*[0 if f is None else f.data_ptr() for f in factors])
         _check("mach_hooi_tucker2", self._lib.mach_hooi_tucker2(self.handle, _int(full), int(keep), int(sweeps),
-                                                                PREC[prec], _ptrs(factors),
+                                                                PREC[prec], fptr,
                                                                 ctypes.c_void_p(G.data_ptr() if G is not None else 0),
                                                                 1 if warm else 0, _stream(stream)))
         return G, factors
