@@ -477,10 +477,20 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
         return release_stream(), fail(s);
       if (from_host && cudaEventRecord(consumed[c & 1], st) != cudaSuccess) return release_stream(), fail(MACH_ECUDA);
     }
-    if ((s = launch_seg_gather(dtype, pl, nseg_all, CE, static_cast<const int64_t*>(seg_cnt.ptr),
-                               static_cast<const uint32_t*>(seg_off.ptr), seg_val.ptr,
-                               static_cast<int64_t*>(h->idx.ptr), h->val.ptr, cap_all, &ds->err, st)) != MACH_OK)
+    // output position of every segment: one exclusive scan of the counts
+    DevBuf seg_scan;
+    if ((s = dev_alloc(seg_scan, (size_t)(nseg_all + scan_tmp_elems_total(nseg_all)) * 8, st)) != MACH_OK)
       return release_stream(), fail(s);
+    long long* cnt_ll = static_cast<long long*>(seg_cnt.ptr);
+    long long* scan_ll = static_cast<long long*>(seg_scan.ptr);
+    if ((s = scan_exclusive<long long>(cnt_ll, scan_ll, nseg_all, nullptr, scan_ll + nseg_all, st)) != MACH_OK)
+      return release_stream(), fail(s);
+    if ((s = launch_seg_gather(dtype, pl, nseg_all, CE, static_cast<const int64_t*>(seg_cnt.ptr),
+                               static_cast<const int64_t*>(seg_scan.ptr), static_cast<const uint32_t*>(seg_off.ptr),
+                               seg_val.ptr, static_cast<int64_t*>(h->idx.ptr), h->val.ptr, cap_all, &ds->err,
+                               st)) != MACH_OK)
+      return release_stream(), fail(s);
+    dev_free(seg_scan, st);
     prof_end(PROF_SAMPLER, st, 0.0);
     std::vector<int64_t> cnt((size_t)nseg_all);
     SampleScalars hs;

@@ -329,10 +329,17 @@ mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, int64_t 
                                const SegPlan& pl, uint32_t* seg_off, void* seg_val, int64_t* seg_count,
                                cudaStream_t st, bool skip);
 // Gathers nseg_total segments: segment c belongs to input chunk c / pl.nseg,
-// whose first linear index is (c / pl.nseg) * chunk_entries.
+// whose first linear index is (c / pl.nseg) * chunk_entries, and starts at
+// output position seg_start[c] (the exclusive scan of seg_count).
 mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, int64_t nseg_total, int64_t chunk_entries,
-                              const int64_t* seg_count, const uint32_t* seg_off, const void* seg_val, int64_t* idx,
-                              void* val, int64_t out_cap, unsigned* d_err, cudaStream_t st);
+                              const int64_t* seg_count, const int64_t* seg_start, const uint32_t* seg_off,
+                              const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
+                              cudaStream_t st);
+// Exclusive scan (sort.cu; instantiated for uint32_t and long long); `tmp`
+// holds scan_tmp_elems_total(n) elements.
+template <typename T>
+mach_status scan_exclusive(const T* in, T* out, int64_t n, T* total_dev, T* tmp, cudaStream_t st);
+int64_t scan_tmp_elems_total(int64_t n);
 int64_t sampler_chunk_align();
 // Tucker2 of a 3-way sample (tucker2.cu).
 struct Tucker2Leaf {

@@ -471,20 +471,14 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm) sample_seg_kernel(
 // copies segment c.  Segments that overflowed their capacity are flagged
 // (the host then reruns with the exact capacity).
 template <typename V>
-__global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restrict__ seg_count, int64_t seg_cap,
+__global__ void __launch_bounds__(256) seg_gather_kernel(const int64_t* __restrict__ seg_count,
+                                                         const int64_t* __restrict__ seg_start, int64_t seg_cap,
                                                          int64_t seg_span, int64_t nseg_chunk, int64_t chunk_entries,
                                                          const uint32_t* __restrict__ seg_off,
                                                          const V* __restrict__ seg_val, int64_t* __restrict__ idx,
                                                          V* __restrict__ val, int64_t out_cap, unsigned* err) {
-  __shared__ int64_t off;
-  const int c = blockIdx.x;
-  if (threadIdx.x < 32) {
-    int64_t s = 0;
-    for (int k = threadIdx.x; k < c; k += 32) s += seg_count[k];
-    s = warp_sum(s);
-    if (threadIdx.x == 0) off = s;
-  }
-  __syncthreads();
+  const int64_t c = blockIdx.x;
+  const int64_t off = seg_start[c];   // exclusive scan of the segment counts
   const int64_t cnt = seg_count[c];
   if (cnt > seg_cap) {
     if (threadIdx.x == 0) atomicOr(err, DEV_OVERFLOW);
@@ -557,17 +551,18 @@ mach_status launch_sampler_seg(const void* x, mach_dtype dt, int64_t n, int64_t 
 }
 
 mach_status launch_seg_gather(mach_dtype dt, const SegPlan& pl, int64_t nseg_total, int64_t chunk_entries,
-                              const int64_t* seg_count, const uint32_t* seg_off, const void* seg_val, int64_t* idx,
-                              void* val, int64_t out_cap, unsigned* d_err, cudaStream_t st) {
+                              const int64_t* seg_count, const int64_t* seg_start, const uint32_t* seg_off,
+                              const void* seg_val, int64_t* idx, void* val, int64_t out_cap, unsigned* d_err,
+                              cudaStream_t st) {
   const int64_t span = pl.chunks_per_seg * kChunk;
   if (dt == MACH_F32)
     seg_gather_kernel<float><<<(unsigned)nseg_total, 256, 0, st>>>(
-        seg_count, pl.seg_cap, span, pl.nseg, chunk_entries, seg_off, static_cast<const float*>(seg_val), idx,
-        static_cast<float*>(val), out_cap, d_err);
+        seg_count, seg_start, pl.seg_cap, span, pl.nseg, chunk_entries, seg_off, static_cast<const float*>(seg_val),
+        idx, static_cast<float*>(val), out_cap, d_err);
   else
     seg_gather_kernel<double><<<(unsigned)nseg_total, 256, 0, st>>>(
-        seg_count, pl.seg_cap, span, pl.nseg, chunk_entries, seg_off, static_cast<const double*>(seg_val), idx,
-        static_cast<double*>(val), out_cap, d_err);
+        seg_count, seg_start, pl.seg_cap, span, pl.nseg, chunk_entries, seg_off,
+        static_cast<const double*>(seg_val), idx, static_cast<double*>(val), out_cap, d_err);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
