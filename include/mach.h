@@ -145,10 +145,10 @@ mach_status mach_sample_skip(const void* x_dev, mach_dtype dtype, int d, const i
                              double p, uint64_t seed, void* stream, mach_sample_t* out);
 
 /* ---------------------------------------------------------------------------
- * mach_sample_noalloc — the same coin and compaction as mach_sample (Section
- * 3 Remark 1; Algorithm 1 and 2, first block), written straight into
- * caller-owned buffers, with NO allocation of any kind: no device or host
- * heap memory, no memory pool, no library routine that allocates.  The paper
+ * mach_sample_noalloc — the same coin and compaction as mach_sample, written
+ * straight into caller-owned buffers, with NO allocation of any kind: no
+ * device or host heap memory, no memory pool, no library routine that
+ * allocates.  The paper
  * has no counterpart; it exists for callers that must not allocate while
  * they sample: a process whose device memory is entirely committed to
  * resident tensors and preallocated output slabs (an allocation would fail
@@ -206,6 +206,27 @@ mach_status mach_sample_fibers(mach_sample_t s, int mode, int64_t* n_fibers);
  * may be NULL. */
 mach_status mach_sample_stats(mach_sample_t s, int64_t* eig_calls, int64_t* eig_iters,
                               int64_t* eig_unconverged, unsigned* device_flags);
+
+/* ---------------------------------------------------------------------------
+ * mach_sample_gram — the Gram X^_(n) X^_(n)^T of the sampled tensor's mode-n
+ * matricization (raw kept values, no 1/p), whose leading eigenvectors are
+ * the HOSVD factor A_n (Section 2.1 HOSVD; Algorithm 1, and Algorithm 2's
+ * initialisation).  mach_hooi computes it to start HOOI; this call exposes
+ * it.
+ *   mode      0 .. d-1.
+ *   method    0: exact, every pair of kept entries of each fibre along mode
+ *             n multiplied and summed in FP64;
+ *             1: tensor cores, BF16 values, FP32 accumulation (relative
+ *             error of a few 2^-9);
+ *             2: tensor cores, each value as a pair of BF16 numbers (about
+ *             16 significant bits), FP32 accumulation.
+ *             Methods 1 and 2 need I_n <= 4096.
+ *   gram_dev  device FP64 buffer of I_n x I_n entries, row-major (written).
+ * Asynchronous on `stream`.  Errors: MACH_EINVAL (arguments), MACH_ENOMEM,
+ * MACH_ECUDA.  A device-side timeout sets the status bits of
+ * mach_sample_stats.
+ */
+mach_status mach_sample_gram(mach_sample_t s, int mode, int method, double* gram_dev, void* stream);
 
 /* Release a sample object and its device memory (synchronises its stream). */
 mach_status mach_sample_free(mach_sample_t s);
@@ -272,10 +293,10 @@ mach_status mach_hooi_tucker2(mach_sample_t s, const int* ranks, int keep_mode, 
  * without returning to the host, which removes the per-mode launches that
  * bound many small decompositions.  Unless warm_start != 0, every factor is
  * first initialised inside the same launch by HOSVD: the r_n leading
- * eigenvectors of X^_(n) X^_(n)^T from 12 block subspace iterations (width
+ * eigenvectors of X^_(n) X^_(n)^T from 40 block subspace iterations (width
  * 16, seeded by the sample's seed) applied through the fibres along mode n,
  * and a Rayleigh-Ritz step (the atomically accumulated products make this
- * start reproducible to rounding only; HOOI refines it).  The sweeps are
+ * start reproducible to rounding only).  The sweeps are
  * FP32: the TTM chain over the mode-n CSF, the
  * Gram of the smaller side of Y_(n) (M = min(I_n, J_n) <= 32), its full
  * eigendecomposition by cyclic Jacobi, A_n = Y V Lambda^-1/2 (or V), then a
@@ -395,6 +416,21 @@ mach_status mach_request_bytes(mach_dtype dtype, int d, const int64_t* dims, con
  * mach_launch_count returns the number of CUDA kernels libmach has launched
  * since it was loaded (all kinds, whether profiling is on or not).
  */
+/* ---------------------------------------------------------------------------
+ * mach_check_bounded_wait — self-check of the bounded device-side wait that
+ * every libmach kernel uses on its barriers (a wait that gives up after a
+ * fixed number of polls, flags a status bit and returns, so that a barrier
+ * that never completes costs an error code rather than a hung GPU).  One
+ * thread block waits on a barrier phase for at most `limit` polls (1 <=
+ * limit <= 2^23; each poll sleeps ~64 ns or more).  arrive != 0: the block
+ * completes the phase itself first and the call returns MACH_OK.  arrive ==
+ * 0: nothing completes it, the wait runs out and the call returns
+ * MACH_ETIMEOUT, with the device context still usable.  Synchronises
+ * `stream`.  Diagnostic; not part of the method.
+ * Errors: MACH_EINVAL (limit outside the range), MACH_ENOMEM, MACH_ECUDA.
+ */
+mach_status mach_check_bounded_wait(long long limit, int arrive, void* stream);
+
 mach_status mach_profile_enable(int enable);
 mach_status mach_profile_query(int kind, double* total_ms, int64_t* launches, double* bytes);
 int64_t mach_launch_count(void);

@@ -272,7 +272,9 @@ __device__ void bat_lsv(const float* Y, int I, int J, int r, float* A, BatShared
 }
 
 constexpr int kHosvdB = 16;     // block width of the HOSVD subspace iteration
-constexpr int kHosvdIt = 12;    // its iteration count (HOOI refines the start)
+constexpr int kHosvdIt = 40;    // its iteration cap (the start of the oracle is the exact HOSVD)
+constexpr int kHosvdCheck = 4;  // Ritz residuals are tested every kHosvdCheck iterations
+constexpr float kHosvdTol = 2e-6f;   // ... against this fraction of the largest Ritz value
 
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -333,37 +335,12 @@ __device__ void bat_gram_apply(const BatMode& src, int rows_src, int I, const fl
   __syncthreads();
 }
 
-// HOSVD start of mode n (Algorithm 2's initialisation): A_n = leading r
-// eigenvectors of X^_(n) X^_(n)^T by kHosvdIt block subspace iterations of
-// width 16 from a seeded random block, then a Rayleigh-Ritz step on the last
-// block (H = V^T C V, Jacobi, A = V Q_r).  Vb, W: I x 16 scratch (16-byte
-// aligned); W is read through L2 only (it is accumulated by atomics).
-template <typename V>
-__device__ void bat_hosvd_mode(const BatMode& src, int rows_src, int I, int r, uint64_t seed, float* Vb, float* W,
-                               float* A, BatShared& sh, unsigned* err) {
+// Rayleigh-Ritz of the block: H = V^T W (W = C V, symmetrised) diagonalised
+// by Jacobi on one warp; sh.C holds the Ritz values on its diagonal, sh.Q
+// the rotation, sh.perm their descending order.  W is read through L2 (it
+// is accumulated by atomics).
+__device__ void bat_block_rr(const float* Vb, const float* W, int I, int bw, BatShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // block width bw = min(16, I); rows of Vb and W have stride 16 (unused
-  // columns are zero).  When I <= 16 the block is the identity, so one
-  // product gives the whole Gram and the Rayleigh-Ritz step is exact.
-  const int bw = min(kHosvdB, I);
-  const bool exact = I <= kHosvdB;
-  for (int e = tid; e < I * kHosvdB; e += kBatThreads) {
-    const int i = e / kHosvdB, c = e - i * kHosvdB;
-    Vb[e] = c >= bw ? 0.f : (exact ? (i == c ? 1.f : 0.f) : start_deviate(seed, (uint64_t)e));
-  }
-  __syncthreads();
-  if (!exact) bat_orth(Vb, I, bw, kHosvdB, Vb, sh, err);
-  for (int it = 0;; ++it) {
-    bat_gram_apply<V>(src, rows_src, I, Vb, W);
-    if (exact || it + 1 == kHosvdIt) break;
-    // V <- orth(W): W is staged into V through L2 first
-    for (int e = tid; e < I * kHosvdB; e += kBatThreads) Vb[e] = __ldcg(W + e);
-    __syncthreads();
-    bat_orth(Vb, I, bw, kHosvdB, Vb, sh, err);
-  }
-  // Rayleigh-Ritz: H = V^T W (symmetrised), eigenvectors Q, A = V Q_r
-  for (int e = tid; e < I * kHosvdB; e += kBatThreads) W[e] = __ldcg(W + e);
-  __syncthreads();
   cross_cols_partial(Vb, W, I, bw, kHosvdB, sh);
   __syncthreads();
   for (int e = tid; e < bw * bw; e += kBatThreads) {
@@ -392,6 +369,100 @@ __device__ void bat_hosvd_mode(const BatMode& src, int rows_src, int I, int r, u
     __syncwarp();
   }
   __syncthreads();
+}
+
+// Whether the leading r Ritz pairs of the last bat_block_rr have residuals
+// ||W q_j - theta_j V q_j|| below kHosvdTol theta_1 (all threads return
+// the same answer).
+__device__ bool bat_ritz_converged(const float* Vb, const float* W, int I, int bw, int r, BatShared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float res[kMaxRank];
+#pragma unroll
+  for (int k = 0; k < kMaxRank; ++k) res[k] = 0.f;
+  for (int i = tid; i < I; i += kBatThreads) {
+    float v[kHosvdB], w[kHosvdB];
+#pragma unroll
+    for (int c = 0; c < kHosvdB; ++c) {
+      v[c] = Vb[(size_t)i * kHosvdB + c];
+      w[c] = __ldcg(W + (size_t)i * kHosvdB + c);
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxRank; ++k) {
+      if (k < r) {
+        const int pk = sh.perm[k];
+        const float th = sh.C[pk * kBatLd + pk];
+        float e = 0.f;
+#pragma unroll
+        for (int c = 0; c < kHosvdB; ++c)
+          if (c < bw) e += (w[c] - th * v[c]) * sh.Q[c * kBatLd + pk];
+        res[k] += e * e;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxRank; ++k) res[k] = warp_sum(res[k]);
+  __shared__ float wres[kBatWarps][kMaxRank];
+  __shared__ int conv;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < kMaxRank; ++k) wres[warp][k] = res[k];
+  __syncthreads();
+  if (tid == 0) {
+    const float th0 = sh.C[sh.perm[0] * kBatLd + sh.perm[0]];
+    float worst = 0.f;
+    for (int k = 0; k < r; ++k) {
+      float t = 0.f;
+      for (int w = 0; w < kBatWarps; ++w) t += wres[w][k];
+      worst = fmaxf(worst, t);
+    }
+    conv = th0 > 0.f && sqrtf(worst) <= kHosvdTol * th0 ? 1 : 0;
+  }
+  __syncthreads();
+  const bool out = conv != 0;
+  __syncthreads();
+  return out;
+}
+
+// HOSVD start of mode n (Algorithm 2's initialisation): A_n = leading r
+// eigenvectors of X^_(n) X^_(n)^T by kHosvdIt block subspace iterations of
+// width 16 from a seeded random block, then a Rayleigh-Ritz step on the last
+// block (H = V^T C V, Jacobi, A = V Q_r).  Vb, W: I x 16 scratch (16-byte
+// aligned); W is read through L2 only (it is accumulated by atomics).
+template <typename V>
+__device__ void bat_hosvd_mode(const BatMode& src, int rows_src, int I, int r, uint64_t seed, float* Vb, float* W,
+                               float* A, BatShared& sh, unsigned* err) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // block width bw = min(16, I); rows of Vb and W have stride 16 (unused
+  // columns are zero).  When I <= 16 the block is the identity, so one
+  // product gives the whole Gram and the Rayleigh-Ritz step is exact.
+  const int bw = min(kHosvdB, I);
+  const bool exact = I <= kHosvdB;
+  for (int e = tid; e < I * kHosvdB; e += kBatThreads) {
+    const int i = e / kHosvdB, c = e - i * kHosvdB;
+    Vb[e] = c >= bw ? 0.f : (exact ? (i == c ? 1.f : 0.f) : start_deviate(seed, (uint64_t)e));
+  }
+  __syncthreads();
+  if (!exact) bat_orth(Vb, I, bw, kHosvdB, Vb, sh, err);
+  bool have_rr = false;
+  for (int it = 0;; ++it) {
+    bat_gram_apply<V>(src, rows_src, I, Vb, W);
+    if (exact || it + 1 == kHosvdIt) break;
+    // every kHosvdCheck iterations: stop once the leading r Ritz pairs have
+    // converged (the Rayleigh-Ritz step below is then the one just made)
+    if (it % kHosvdCheck == kHosvdCheck - 1) {
+      bat_block_rr(Vb, W, I, bw, sh);
+      if (bat_ritz_converged(Vb, W, I, bw, r, sh)) {
+        have_rr = true;
+        break;
+      }
+    }
+    // V <- orth(W): W is staged into V through L2 first
+    for (int e = tid; e < I * kHosvdB; e += kBatThreads) Vb[e] = __ldcg(W + e);
+    __syncthreads();
+    bat_orth(Vb, I, bw, kHosvdB, Vb, sh, err);
+  }
+  // Rayleigh-Ritz: H = V^T W (symmetrised), eigenvectors Q, A = V Q_r
+  if (!have_rr) bat_block_rr(Vb, W, I, bw, sh);
   for (int i = tid; i < I; i += kBatThreads) {
     float v[kHosvdB];
 #pragma unroll

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <type_traits>
 #include <vector>
 
 namespace mach {
@@ -361,6 +362,11 @@ mach_status mach_profile_query(int kind, double* total_ms, int64_t* launches, do
 
 int64_t mach_launch_count(void) { return (int64_t)g_launches.load(); }
 
+mach_status mach_check_bounded_wait(long long limit, int arrive, void* stream) {
+  if (limit < 1 || limit > kSpinLimit) return MACH_EINVAL;
+  return run_bounded_wait_check(limit, arrive, static_cast<cudaStream_t>(stream));
+}
+
 // The input streamed from host memory: chunk_entries > 0 entries of x_host
 // at a time, copied into a ring of two device buffers on a copy stream while
 // the sampler runs on the previous chunk.
@@ -414,7 +420,7 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
   const int64_t nchunks = from_host ? ceil_div(N, CE) : 1;
   SegPlan pl = plan_segments(CE, dtype, q);
   const size_t vs = dtype_size(dtype);
-  DevBuf ring[2];
+  ScopedDevBuf ring[2] = {ScopedDevBuf(st), ScopedDevBuf(st)};
   cudaStream_t cst = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
   auto release_stream = [&]() {
@@ -423,7 +429,10 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
       if (consumed[b]) cudaEventDestroy(consumed[b]);
       copied[b] = consumed[b] = nullptr;
     }
-    if (cst) cudaStreamDestroy(cst);
+    if (cst) {
+      cudaStreamSynchronize(cst);   // no copy into the ring is left in flight
+      cudaStreamDestroy(cst);
+    }
     cst = nullptr;
   };
   if (from_host) {
@@ -445,7 +454,7 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
     }
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
-    DevBuf seg_off, seg_val, seg_cnt;
+    ScopedDevBuf seg_off(st), seg_val(st), seg_cnt(st);
     const int64_t nseg_all = pl.nseg * nchunks;
     const int64_t cap_all = nseg_all * pl.seg_cap;
     if ((s = dev_alloc(h->idx, (size_t)cap_all * 8, st)) != MACH_OK) return release_stream(), fail(s);
@@ -478,7 +487,7 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
       if (from_host && cudaEventRecord(consumed[c & 1], st) != cudaSuccess) return release_stream(), fail(MACH_ECUDA);
     }
     // output position of every segment: one exclusive scan of the counts
-    DevBuf seg_scan;
+    ScopedDevBuf seg_scan(st);
     if ((s = dev_alloc(seg_scan, (size_t)(nseg_all + scan_tmp_elems_total(nseg_all)) * 8, st)) != MACH_OK)
       return release_stream(), fail(s);
     long long* cnt_ll = static_cast<long long*>(seg_cnt.ptr);
@@ -536,7 +545,7 @@ static mach_status sample_impl(const void* x_dev, mach_dtype dtype, int d, const
   h->mode[0].val = h->val;
   int64_t maxdim = 1;
   for (int k = 0; k < d; ++k) maxdim = std::max(maxdim, h->dims[k]);
-  DevBuf sort_scr, csf_scr;
+  ScopedDevBuf sort_scr(st), csf_scr(st);
   if ((s = dev_alloc(sort_scr, sort_scratch_bytes(K, maxdim), st)) != MACH_OK) return fail(s);
   if ((s = dev_alloc(csf_scr, csf_scratch_bytes(K, maxdim), st)) != MACH_OK) return fail(s);
   const int64_t Kc = std::max<int64_t>(K, 1);
@@ -757,7 +766,7 @@ mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
   MACH_TRY(dev_alloc(w.V, (size_t)maxM * 32 * sizeof(T), st));
   MACH_TRY(dev_alloc(w.W, (size_t)maxM * 32 * sizeof(T), st));
   MACH_TRY(dev_alloc(w.U, (size_t)maxM * 32 * sizeof(T), st));
-  MACH_TRY(dev_alloc(w.Vout, (size_t)maxM * kMaxRank * sizeof(double), st));
+  MACH_TRY(dev_alloc(w.Vout, eig_out_bytes((int)maxM), st));
   MACH_TRY(dev_alloc(w.theta, (size_t)32 * sizeof(double), st));
   MACH_TRY(dev_alloc(w.A64, (size_t)maxIr * sizeof(double), st));
   // per-CTA partial Grams of the FP64 Cholesky QR (lsv_finish grid <= 2 SMs worth)
@@ -767,6 +776,17 @@ mach_status ensure_ws(mach_sample_s* h, const int* ranks, Workspace& w) {
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.fac[k], (size_t)h->dims[k] * ranks[k] * sizeof(T) + 64, st));
   for (int k = 0; k < d; ++k) MACH_TRY(dev_alloc(w.basis[k], (size_t)maxM * 32 * sizeof(T), st));
   MACH_TRY(dev_alloc(w.eig_part, eig_part_elems((int)maxM) * sizeof(T), st));
+#ifdef MACH_POISON_WS
+  // debugging aid: every workspace word starts as a NaN, so that a read of a
+  // word no kernel has written shows in the results
+  {
+    DevBuf* bufs[] = {&w.Y, &w.partial, &w.C, &w.gram_part, &w.V, &w.W, &w.U, &w.Vout, &w.theta, &w.A64,
+                      &w.gram64, &w.ytpart, &w.rinv, &w.eig_part, &w.fac[0], &w.fac[1], &w.fac[2], &w.fac[3],
+                      &w.basis[0], &w.basis[1], &w.basis[2], &w.basis[3]};
+    for (DevBuf* b : bufs)
+      if (b->ptr) MACH_CUDA_TRY(cudaMemsetAsync(b->ptr, 0xFF, b->bytes, st));
+  }
+#endif
   for (int k = 0; k < d; ++k) w.ranks[k] = ranks[k];
   w.ready = true;
   (void)maxI;
@@ -850,38 +870,76 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   e.part = w.eig_part.ptr;
   e.stats = h->dscal()->eig_stats;
   e.basis_out = w.basis[n].ptr;
-  e.rr = static_cast<double*>(w.gram64.ptr);
+  e.rr = static_cast<double*>(w.Vout.ptr);   // the split path's rotation (the factor kernel reads it)
+  e.ctl = h->dscal()->eig_ctl;
   MACH_TRY(launch_eig<T>(static_cast<const T*>(w.C.ptr), e, st));
-  return launch_lsv_finish<T>(Y, e.Vout, e.theta, I, J, r, jroute,
+  return launch_lsv_finish<T>(Y, eig_result<T>(e), I, J, r, jroute,
                               static_cast<double*>(w.A64.ptr), static_cast<double*>(w.gram64.ptr),
                               &h->dscal()->counter, static_cast<double*>(w.rinv.ptr), &h->dscal()->err, fac_out,
                               static_cast<T*>(w.fac[n].ptr), st);
 }
 
-// HOSVD of X^: A_n = leading eigenvectors of X^_(n) X^_(n)^T, from the
-// fibres along mode n (the CSF whose leaf is n: mode (n + 1) mod d).
+// The HOSVD Gram of mode n, X^_(n) X^_(n)^T (raw values), from the fibres
+// along mode n (the CSF whose leaf is n: mode (n + 1) mod d), into C (I_n x
+// I_n row-major).  method 0: exact, every pair of kept entries of a fibre
+// accumulated in T; 1 / 2: on the tensor cores with 1 / 2 BF16 terms
+// (T = float only).
+template <typename T>
+mach_status hosvd_gram(mach_sample_s* h, int n, int method, T* C, cudaStream_t st) {
+  const int d = h->d;
+  const int src = (n + 1) % d;
+  const ModeCsf& M = h->mode[src];
+  const int In = (int)h->dims[n];
+  if (method > 0) {
+    ScopedDevBuf scr(st);
+    MACH_TRY(dev_alloc(scr, tc_gram_scratch_bytes(In), st));
+    return launch_tc_gram<T>(M.val.ptr, h->dt, static_cast<const uint16_t*>(M.leaf.ptr),
+                             static_cast<const uint32_t*>(M.fib_start.ptr), h->nfib[src], In, method,
+                             static_cast<float*>(scr.ptr), C, &h->dscal()->err, st);
+  }
+  if (h->dt == MACH_F32)
+    return launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                      static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src], h->K, In,
+                                      C, st);
+  return launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
+                                     static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src], h->K, In,
+                                     C, st);
+}
+
+// Keep probability from which the HOSVD Gram of the FP32 sweeps runs on the
+// tensor cores: the dense tile work grows like I N and the pairwise
+// products like p^2 I N, so the tiles win once a few percent are kept.
+constexpr double kTcGramMinP = 0.02;
+
+// Method of the HOSVD Gram that starts HOOI: the tensor cores for FP32 sweeps
+// (2 BF16 terms; 1 for BF16_REFINE) when sweeps follow to refine the start
+// and the sample is dense enough; else the exact pairwise sums.
+template <typename T>
+int hosvd_gram_method(const mach_sample_s* h, int n, int sweeps, bool bf16) {
+  if (!std::is_same<T, float>::value || sweeps <= 0 || h->p < kTcGramMinP) return 0;
+  if (h->dims[n] > tc_gram_max_order()) return 0;
+  return bf16 ? 1 : 2;
+}
+
+// Iteration cap of the HOSVD eigensolve (it stops earlier once the Ritz
+// residuals meet the path's tolerance; FP64 on long modes runs the cap).
+// HOOI stopped after a fixed number of sweeps depends on its start, so with
+// few sweeps to follow the start must be the HOSVD itself (up to 40
+// iterations; 400 for MACH-HOSVD alone).  With 15 or more sweeps HOOI's own
+// contraction removes the start's error (at 1000^3 with 20 sweeps, starts
+// 8 and 40 iterations in give the same result to rounding), so 8 suffice.
+inline int hosvd_iterations(int sweeps) { return sweeps <= 0 ? 400 : sweeps >= 15 ? 8 : 40; }
+
+// HOSVD of X^: A_n = leading eigenvectors of X^_(n) X^_(n)^T.
 template <typename T>
 mach_status hosvd_start(mach_sample_s* h, Workspace& w, const int* ranks, int sweeps, double* const* factors,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool bf16 = false) {
   const int d = h->d;
   for (int n = 0; n < d; ++n) {
-    const int src = (n + 1) % d;
-    const ModeCsf& M = h->mode[src];
     const int In = (int)h->dims[n];
     prof_begin(PROF_INITGRAM, st);
-    if (h->dt == MACH_F32)
-      MACH_TRY((launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
-                                           static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
-                                           h->K, In, static_cast<T*>(w.C.ptr), st)));
-    else
-      MACH_TRY((launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
-                                            static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src],
-                                            h->K, In, static_cast<T*>(w.C.ptr), st)));
-    // With sweeps to follow, HOOI refines the start, so the HOSVD Gram's
-    // eigenvectors are iterated at most 40 times (FP64) or 8 times (FP32,
-    // whose results are compared at 1e-5); MACH-HOSVD alone (no sweeps)
-    // iterates to convergence (at most 400).
-    const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 8) : 400;
+    MACH_TRY(hosvd_gram<T>(h, n, hosvd_gram_method<T>(h, n, sweeps, bf16), static_cast<T*>(w.C.ptr), st));
+    const int init_it = hosvd_iterations(sweeps);
     MACH_TRY(solve_factor<T>(h, w, n, ranks[n], In, In, false, false, init_it, factors[n], st));
     prof_end(PROF_INITGRAM, st, 0.0);
   }
@@ -982,7 +1040,7 @@ mach_status hooi_impl(mach_sample_s* h, const int* ranks, int sweeps, double* co
       MACH_TRY(launch_factor_to_rowmajor<T>(factors[k], (int)h->dims[k], ranks[k], static_cast<T*>(w.fac[k].ptr),
                                             st));
   } else {
-    MACH_TRY(hosvd_start<T>(h, w, ranks, sweeps, factors, st));
+    MACH_TRY(hosvd_start<T>(h, w, ranks, sweeps, factors, st, bf16));
   }
   if (bf16 && sweeps > 0) {
     for (int n = 0; n < d; ++n) {
@@ -1071,18 +1129,10 @@ mach_status tucker2_impl(mach_sample_s* h, const int* ranks, int c, int sweeps, 
         return done(s);
   } else {
     for (int q = 0; q < 2; ++q) {
-      const int n = cm[q], src = (n + 1) % 3, In = (int)h->dims[n];
-      const ModeCsf& M = h->mode[src];
-      if (h->dt == MACH_F32)
-        s = launch_init_gram<float, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
-                                       static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src], h->K,
-                                       In, static_cast<T*>(w.C.ptr), st);
-      else
-        s = launch_init_gram<double, T>(M.val.ptr, static_cast<const uint16_t*>(M.leaf.ptr),
-                                        static_cast<const uint32_t*>(M.fib_start.ptr), &h->dscal()->nfib[src], h->K,
-                                        In, static_cast<T*>(w.C.ptr), st);
+      const int n = cm[q], In = (int)h->dims[n];
+      s = hosvd_gram<T>(h, n, hosvd_gram_method<T>(h, n, sweeps, false), static_cast<T*>(w.C.ptr), st);
       if (s != MACH_OK) return done(s);
-      const int init_it = sweeps > 0 ? (sizeof(T) == 8 ? 40 : 8) : 400;
+      const int init_it = hosvd_iterations(sweeps);
       if ((s = solve_factor<T>(h, w, n, ranks[n], In, In, false, false, init_it, factors[n], st)) != MACH_OK)
         return done(s);
     }
@@ -1292,6 +1342,21 @@ mach_status mach_hooi_batched(const mach_sample_t* samples, int B, const int* ra
   dev_free(items_dev, st);
   dev_free(ws, st);
   return s;
+}
+
+mach_status mach_sample_gram(mach_sample_t s, int mode, int method, double* gram_dev, void* stream) {
+  if (!s || !gram_dev || mode < 0 || mode >= s->d || method < 0 || method > 2) return MACH_EINVAL;
+  if (method > 0 && s->dims[mode] > tc_gram_max_order()) {
+    set_last_error("tensor-core Gram: I_n = %lld above %d", (long long)s->dims[mode], tc_gram_max_order());
+    return MACH_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s->stream = st;
+  if (s->K == 0)
+    return cudaMemsetAsync(gram_dev, 0, sizeof(double) * (size_t)(s->dims[mode] * s->dims[mode]), st) == cudaSuccess
+               ? MACH_OK
+               : MACH_ECUDA;
+  return hosvd_gram<double>(s, mode, method, gram_dev, st);
 }
 
 mach_status mach_core(mach_sample_t s, const int* ranks, double* const* factors_dev, double* core_dev,

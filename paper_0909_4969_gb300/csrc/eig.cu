@@ -460,20 +460,20 @@ __device__ void apply_rows(const T* X, const T* S, int b, int ncols, T* Out, int
 
 // Final Rayleigh-Ritz of the leading r Ritz vectors in FP64: rr_refine in jacobi.cuh.
 
-// Vout (M x r, row-major FP64) = U_r X with the columns in descending
-// order of lambda; theta = the sorted lambda.
+// The eigenvectors are U_r X: U_r (the leading r Ritz vectors, M x r in the
+// path's precision) is written to Ur (row-major, ld r) and the FP64 rotation
+// X (r x r, columns in descending order of lambda) to Xr, row-major; theta =
+// the sorted lambda.  The product U_r X is formed by the factor kernel
+// (launch_lsv_finish), which spreads its FP64 work over many CTAs.
 template <typename T>
-__device__ void rr_write(const T* U, int ld, int M, int r, const FinalRR& f, double* Vout, double* theta) {
-  // one thread per entry (i, j); each sum over k runs in the same order as
-  // a row-at-a-time loop
+__device__ void rr_write(const T* U, int ld, int M, int r, const FinalRR& f, T* Ur, double* Xr, double* theta) {
   for (int e = threadIdx.x; e < M * r; e += blockDim.x) {
     const int i = e / r, j = e - (e / r) * r;
-    const int pj = f.perm[j];
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < kMaxRank; ++k)
-      if (k < r) s += (double)U[(size_t)i * ld + k] * f.X[k * kRl + pj];
-    Vout[(size_t)i * r + j] = s;
+    Ur[e] = U[(size_t)i * ld + j];
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int k = e / r, j = e - (e / r) * r;
+    Xr[e] = f.X[k * kRl + f.perm[j]];
   }
   if (threadIdx.x < r) theta[threadIdx.x] = f.lam[f.perm[threadIdx.x]];
   __syncthreads();
@@ -482,7 +482,8 @@ __device__ void rr_write(const T* U, int ld, int M, int r, const FinalRR& f, dou
 // General form: H = U_r^T CU_r and G = U_r^T U_r by FP64 sums over the M
 // rows (U, CU row-major with leading dimension ld), then refinement.
 template <typename T>
-__device__ void final_rr(const T* U, const T* CU, int M, int ld, int r, double* Vout, double* theta, FinalRR& f) {
+__device__ void final_rr(const T* U, const T* CU, int M, int ld, int r, T* Ur, double* Xr, double* theta,
+                         FinalRR& f) {
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int p = e / r, q = e - (e / r) * r;
     double h = 0.0, g = 0.0;
@@ -501,7 +502,13 @@ __device__ void final_rr(const T* U, const T* CU, int M, int ld, int r, double* 
   }
   __syncthreads();
   rr_refine(f, r);
-  rr_write<T>(U, ld, M, r, f, Vout, theta);
+  rr_write<T>(U, ld, M, r, f, Ur, Xr, theta);
+}
+
+// U_r of the fused path lives after X (r x r doubles) in the output area.
+template <typename T>
+__host__ __device__ inline T* eig_out_u(double* out, int r) {
+  return reinterpret_cast<T*>(out + kMaxRank * kMaxRank);
 }
 
 template <typename T>
@@ -512,7 +519,7 @@ struct EigArgs {
   T* W;                // M x b scratch (global)
   T* U;                // M x b scratch (global)
   T* part;             // split path: partial b x b Grams, >= 3 * nblk * b * b
-  double* Vout;        // M x r FP64 eigenvectors (row-major)
+  double* Vout;        // output area: X (r x r FP64), then U_r (M x r, T)
   double* theta;       // r FP64 eigenvalues, descending
   int maxit;
   double tol;
@@ -630,11 +637,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     }
     __syncthreads();
     rr_refine(frr, r);
-    rr_write<T>(U, ld, M, r, frr, a.Vout, a.theta);
+    rr_write<T>(U, ld, M, r, frr, eig_out_u<T>(a.Vout, r), a.Vout, a.theta);
   } else {
     tile_gemm<T>(C, ldc, U, ld, M, M, r, W, ld, nullptr);        // C U_r
     __syncthreads();
-    final_rr<T>(U, W, M, ld, r, a.Vout, a.theta, frr);
+    final_rr<T>(U, W, M, ld, r, eig_out_u<T>(a.Vout, r), a.Vout, a.theta, frr);
   }
   if (threadIdx.x == 0 && a.stats) {
     atomicAdd(&a.stats[0], 1ull);
@@ -646,7 +653,13 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
 // ----------------------------------------------------------------------------
 // Split path (large M): fixed iteration count, multi-CTA passes.
 // ----------------------------------------------------------------------------
+// Control words of the split path's early exit (device): [0] converged
+// (the remaining iterations' launches return at once), [1] the iteration
+// whose basis holds the Ritz vectors, [2] the previous residual (double bits).
+__device__ __forceinline__ bool split_done(const unsigned long long* ctl) { return ctl && ctl[0] != 0ull; }
+
 constexpr int kRowsPerCta = 32;
+constexpr int kSplitCheck = 4;   // split path: Ritz residuals tested every 4 iterations
 // W = C V (first nc columns): 64-row x 32-column output tiles with the k
 // range split over gridDim.y (kCvSplit slices).  Tiles of C (stored
 // transposed, so that a thread's 8 rows at one k are contiguous) and of V
@@ -657,7 +670,8 @@ constexpr int kCvRows = 64, kCvK = 32, kCvSplit = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256) cv_tiled_kernel(const T* __restrict__ C, int M, const T* __restrict__ V, int b,
-                                                       int nc, T* __restrict__ P) {
+                                                       int nc, T* __restrict__ P, const unsigned long long* ctl) {
+  if (split_done(ctl)) return;
   __shared__ __align__(16) T Ct[kCvK][kCvRows + 16 / sizeof(T)];
   __shared__ T Vs[kCvK][kB + 1];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -701,7 +715,9 @@ __global__ void __launch_bounds__(256) cv_tiled_kernel(const T* __restrict__ C, 
 }
 
 template <typename T>
-__global__ void cv_reduce_kernel(const T* __restrict__ P, int nsplit, int M, int nc, T* __restrict__ W, int ldw) {
+__global__ void cv_reduce_kernel(const T* __restrict__ P, int nsplit, int M, int nc, T* __restrict__ W, int ldw,
+                                 const unsigned long long* ctl) {
+  if (split_done(ctl)) return;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= M * nc) return;
   const int i = o / nc, j = o - (o / nc) * nc;
@@ -710,12 +726,34 @@ __global__ void cv_reduce_kernel(const T* __restrict__ P, int nsplit, int M, int
   W[(size_t)i * ldw + j] = s;
 }
 
-// partial Grams of a row block: part[blk][0] = V^T W, part[blk][1] = W^T W
+// partial Grams of a row block: part[blk][0] = V^T W, part[blk][1] = W^T W;
+// with part64, also V^T V, V^T W and W^T W summed in FP64 (exact products of
+// the stored values), from which the residual of the subspace is formed
+// without cancellation in the path's precision
 template <typename T>
-__global__ void __launch_bounds__(256) split_grams_kernel(const T* V, const T* W, int M, int b, T* part) {
-  const int i0 = blockIdx.x * kRowsPerCta;
+__global__ void __launch_bounds__(256) split_grams_kernel(const T* V, const T* W, int M, int b, T* part,
+                                                          double* part64, const unsigned long long* ctl) {
+  if (split_done(ctl)) return;
+  const int i0 = blockIdx.x * kRowsPerCta, i1 = min(M, i0 + kRowsPerCta);
   T* h = part + (size_t)blockIdx.x * 2 * b * b;
-  grams_rows<T>(V, W, b, b, i0, min(M, i0 + kRowsPerCta), h, h + b * b, b);
+  grams_rows<T>(V, W, b, b, i0, i1, h, h + b * b, b);
+  if (part64) {
+    double* g = part64 + (size_t)blockIdx.x * 3 * b * b;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+      const int p = e / b, q = e - (e / b) * b;
+      double vv = 0.0, vw = 0.0, ww = 0.0;
+      for (int i = i0; i < i1; ++i) {
+        const double vp = (double)V[(size_t)i * b + p], vq = (double)V[(size_t)i * b + q];
+        const double wp = (double)W[(size_t)i * b + p], wq = (double)W[(size_t)i * b + q];
+        vv += vp * vq;
+        vw += vp * wq;
+        ww += wp * wq;
+      }
+      g[e] = vv;
+      g[b * b + e] = vw;
+      g[2 * b * b + e] = ww;
+    }
+  }
 }
 
 // partial start Gram V^T V of a row block
@@ -728,9 +766,12 @@ __global__ void __launch_bounds__(256) split_gram_vv_kernel(const T* V, int M, i
 // one CTA: reduce partials (fixed order), b-space step; S to global (b x b)
 template <typename T>
 __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nblk, int b, int r, int mode,
-                                                           T* S_out, double* rr_out) {
+                                                           T* S_out, double* rr_out, const double* part64,
+                                                           unsigned long long* ctl, int it, double tol) {
   // mode 0: start block orthonormalisation (part holds V^T V)
-  // mode 1: iteration (next basis); mode 2: final (Ritz rotation)
+  // mode 1: iteration (next basis, or the Ritz rotation once converged);
+  // mode 2: final (Ritz rotation)
+  if (mode != 0 && split_done(ctl)) return;
   __shared__ BSpace<T> bs;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     T h = T(0), g = T(0);
@@ -775,16 +816,80 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
     }
   }
   __syncthreads();
+  bool final_rot = mode == 2;
   if (mode != 0) {
     __shared__ double prev;
-    if (threadIdx.x == 0) prev = 1e300;
-    bspace_step<T>(bs, b, r, 0.0, &prev, false, mode == 2);
+    __shared__ double G64[kB * kLd], L64[kB * kLd], H64[kB * kLd];
+    const bool check = part64 != nullptr;
+    if (check) {
+      // F = W^T (I - P_V) W = P - H^T G^-1 H from the FP64 sums, G = V^T V:
+      // the part of C V outside span(V), exact to FP64 rounding even when V
+      // is orthonormal only to the path's precision
+      for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        double g = 0.0, h = 0.0, pp = 0.0;
+        for (int k = 0; k < nblk; ++k) {
+          const double* q = part64 + (size_t)k * 3 * b * b;
+          g += q[e];
+          h += q[b * b + e];
+          pp += q[2 * b * b + e];
+        }
+        const int p = e / b, q2 = e - (e / b) * b;
+        G64[p * kLd + q2] = g;
+        H64[p * kLd + q2] = h;
+        L64[p * kLd + q2] = pp;   // P until F is formed
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        // lower Cholesky G = L L^T in place (one warp; G is near the identity)
+        const int lane = threadIdx.x;
+        for (int j = 0; j < b; ++j) {
+          if (lane == 0) {
+            double d = G64[j * kLd + j];
+            for (int k = 0; k < j; ++k) d -= G64[j * kLd + k] * G64[j * kLd + k];
+            G64[j * kLd + j] = d > 0.0 ? sqrt(d) : 1e-300;
+          }
+          __syncwarp();
+          for (int i = j + 1 + lane; i < b; i += 32) {
+            double v = G64[i * kLd + j];
+            for (int k = 0; k < j; ++k) v -= G64[i * kLd + k] * G64[j * kLd + k];
+            G64[i * kLd + j] = v / G64[j * kLd + j];
+          }
+          __syncwarp();
+        }
+        // Z = L^-1 H, column per lane (forward substitution), into H64
+        for (int c = lane; c < b; c += 32) {
+          for (int i = 0; i < b; ++i) {
+            double v = H64[i * kLd + c];
+            for (int k = 0; k < i; ++k) v -= G64[i * kLd + k] * H64[k * kLd + c];
+            H64[i * kLd + c] = v / G64[i * kLd + i];
+          }
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int p = e / b, q2 = e - (e / b) * b;
+        double f = L64[p * kLd + q2];
+        for (int k = 0; k < b; ++k) f -= H64[k * kLd + p] * H64[k * kLd + q2];
+        bs.F[p * kLd + q2] = (T)f;
+      }
+      if (threadIdx.x == 0) prev = __longlong_as_double((long long)ctl[2]);
+    } else if (threadIdx.x == 0) {
+      prev = 1e300;
+    }
+    __syncthreads();
+    bspace_step<T>(bs, b, r, check ? tol : 0.0, &prev, check, mode == 2);
+    if (check && bs.conv) final_rot = true;
+    if (check && threadIdx.x == 0) ctl[2] = (unsigned long long)__double_as_longlong(prev);
   }
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int p = e / b, q = e - (e / b) * b;
     S_out[p * kB + q] = bs.S[p * kLd + q];
   }
-  if (mode == 2) {
+  if (final_rot && ctl && threadIdx.x == 0) {
+    ctl[1] = (unsigned long long)it;
+    ctl[0] = 1ull;
+  }
+  if (final_rot) {
     // final FP64 Rayleigh-Ritz of U_r = V S_r from the b-space quantities:
     // H_r = (S^T H S)[:r, :r] (the Jacobi-rotated H), G_r = S_r^T S_r
     __shared__ FinalRR frr;
@@ -807,37 +912,31 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
   }
 }
 
-// Vout = U_r X (FP64, M x r row-major) and theta from rr_out; counts the solve.
-template <typename T>
-__global__ void split_vout_kernel(const T* __restrict__ U, int M, int b, int r, const double* __restrict__ rr_out,
-                                  double* __restrict__ Vout, double* __restrict__ theta,
-                                  unsigned long long* stats, int iters) {
-  __shared__ double X[kMaxRank * kMaxRank];
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) X[e] = rr_out[e];
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < M) {
-    double u[kMaxRank];
-#pragma unroll
-    for (int k = 0; k < kMaxRank; ++k) u[k] = k < r ? (double)U[(size_t)i * b + k] : 0.0;
-    for (int j = 0; j < r; ++j) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < kMaxRank; ++k)
-        if (k < r) s += u[k] * X[k * r + j];
-      Vout[(size_t)i * r + j] = s;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x < r) theta[threadIdx.x] = rr_out[r * r + threadIdx.x];
-  if (blockIdx.x == 0 && threadIdx.x == 0 && stats) {
+// theta from rr_out (its X stays there for the factor kernel); counts the solve.
+__global__ void split_finish_kernel(int r, const double* __restrict__ rr_out, double* __restrict__ theta,
+                                    unsigned long long* stats, int iters, const unsigned long long* ctl) {
+  if (ctl) iters = (int)ctl[1] + 1;
+  if (threadIdx.x < r) theta[threadIdx.x] = rr_out[r * r + threadIdx.x];
+  if (threadIdx.x == 0 && stats) {
     atomicAdd(&stats[0], 1ull);
     atomicAdd(&stats[1], (unsigned long long)iters);
   }
 }
 
-// Out = X S (rows of the CTA's block), S from global (b x b, ld kB)
+__global__ void split_ctl_init(unsigned long long* ctl) {
+  if (threadIdx.x < 2) ctl[threadIdx.x] = 0ull;
+  if (threadIdx.x == 2) ctl[2] = (unsigned long long)__double_as_longlong(1e300);   // no previous residual
+}
+
+// Out = X S (rows of the CTA's block), S from global (b x b, ld kB).  With
+// ctl: skipped once converged (sel == 0), or (sel == 1) X = X1 when the
+// converged iteration ctl[1] is odd (the ping-pong of the bases).
 template <typename T>
-__global__ void __launch_bounds__(256) split_apply_kernel(const T* X, const T* S, int M, int b, T* Out) {
+__global__ void __launch_bounds__(256) split_apply_kernel(const T* X, const T* S, int M, int b, T* Out,
+                                                          const unsigned long long* ctl = nullptr, int sel = 0,
+                                                          const T* X1 = nullptr) {
+  if (sel == 0 && split_done(ctl)) return;
+  if (sel == 1 && (ctl[1] & 1ull)) X = X1;
   __shared__ T Ss[kB * kLd];
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int p = e / b, q = e - (e / b) * b;
@@ -862,7 +961,10 @@ int eig_split_threshold() { return kEigSmallMax; }
 // split-path scratch: per-row-block partial Grams, the b x b transform S,
 // and the k-split partial tiles of C V
 size_t eig_part_elems(int M) {
-  return (size_t)ceil_div(M, kRowsPerCta) * 2 * kB * kB + kB * kB + (size_t)kCvSplit * M * kB;
+  // T partials, S, the C V slices, then (16-byte aligned) the FP64 partials
+  // of the convergence test, counted in 4-byte elements
+  return (size_t)ceil_div(M, kRowsPerCta) * 2 * kB * kB + kB * kB + (size_t)kCvSplit * M * kB + 8 +
+         (size_t)ceil_div(M, kRowsPerCta) * 3 * kB * kB * 2;
 }
 
 template <typename T>
@@ -905,54 +1007,95 @@ mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st) {
     MACH_LAUNCH_CHECK();
     return MACH_OK;
   }
-  // split path: V0 -> orthonormal V; fixed iterations; final rotation and FP64 Rayleigh-Ritz
+  // split path: V0 -> orthonormal V; iterations (FP32: with a convergence
+  // test and an early exit on the device, every later launch returning at
+  // once; FP64: a fixed count); final rotation and FP64 Rayleigh-Ritz
   const int nblk = (int)ceil_div(M, kRowsPerCta);
   T* part = a.part;
   T* S = part + (size_t)nblk * 2 * b * b;
   T* cvp = S + kB * kB;
-  T* V = a.V;
-  T* W = a.W;
-  T* U = a.U;
+  const bool check = sizeof(T) == 4 && e.ctl != nullptr;
+  double* part64 = nullptr;
+  if (check) {
+    uintptr_t p64 = reinterpret_cast<uintptr_t>(cvp + (size_t)kCvSplit * M * kB);
+    p64 = (p64 + 15) & ~(uintptr_t)15;
+    part64 = reinterpret_cast<double*>(p64);
+  }
+  unsigned long long* ctl = check ? e.ctl : nullptr;
   const dim3 cv_grid((unsigned)ceil_div(M, kCvRows), kCvSplit);
   const unsigned red_grid = (unsigned)ceil_div((int64_t)M * b, 256);
-  split_gram_vv_kernel<T><<<nblk, 256, 0, st>>>(V, M, b, part);
+  if (ctl) {
+    split_ctl_init<<<1, 32, 0, st>>>(ctl);
+    MACH_LAUNCH_CHECK();
+  }
+  split_gram_vv_kernel<T><<<nblk, 256, 0, st>>>(a.V, M, b, part);
   MACH_LAUNCH_CHECK();
-  split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, 0, S, e.rr);
+  split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, 0, S, e.rr, nullptr, nullptr, 0, 0.0);
   MACH_LAUNCH_CHECK();
-  split_apply_kernel<T><<<nblk, 256, 0, st>>>(V, S, M, b, W);
+  split_apply_kernel<T><<<nblk, 256, 0, st>>>(a.V, S, M, b, a.U);
   MACH_LAUNCH_CHECK();
-  std::swap(V, W);
+  T* Vb[2] = {a.U, a.V};   // the orthonormal start is in U; the bases alternate
+  T* W = a.W;
   const int iters = std::max(1, e.maxit);
   for (int it = 0; it < iters; ++it) {
-    cv_tiled_kernel<T><<<cv_grid, 256, 0, st>>>(C, M, V, b, b, cvp);
+    T* Vc = Vb[it & 1];
+    T* Vn = Vb[(it + 1) & 1];
+    cv_tiled_kernel<T><<<cv_grid, 256, 0, st>>>(C, M, Vc, b, b, cvp, ctl);
     MACH_LAUNCH_CHECK();
-    cv_reduce_kernel<T><<<red_grid, 256, 0, st>>>(cvp, kCvSplit, M, b, W, b);
+    cv_reduce_kernel<T><<<red_grid, 256, 0, st>>>(cvp, kCvSplit, M, b, W, b, ctl);
     MACH_LAUNCH_CHECK();
-    split_grams_kernel<T><<<nblk, 256, 0, st>>>(V, W, M, b, part);
+    // the residual test (FP64 Grams) every kSplitCheck-th iteration
+    const bool test = ctl && it % kSplitCheck == kSplitCheck - 1 && it + 1 < iters;
+    split_grams_kernel<T><<<nblk, 256, 0, st>>>(Vc, W, M, b, part, test ? part64 : nullptr, ctl);
     MACH_LAUNCH_CHECK();
     const bool last = it + 1 == iters;
-    split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, last ? 2 : 1, S, e.rr);
+    split_bspace_kernel<T><<<1, 256, 0, st>>>(part, nblk, b, e.r, last ? 2 : 1, S, e.rr, test ? part64 : nullptr,
+                                              ctl, it, e.tol);
     MACH_LAUNCH_CHECK();
-    if (last) {
-      split_apply_kernel<T><<<nblk, 256, 0, st>>>(V, S, M, b, U);   // Ritz vectors
+    if (ctl) {
+      split_apply_kernel<T><<<nblk, 256, 0, st>>>(W, S, M, b, Vn, ctl, 0);   // next basis, until converged
       MACH_LAUNCH_CHECK();
-    } else {
-      split_apply_kernel<T><<<nblk, 256, 0, st>>>(W, S, M, b, U);   // next basis
+    } else if (!last) {
+      split_apply_kernel<T><<<nblk, 256, 0, st>>>(W, S, M, b, Vn);
       MACH_LAUNCH_CHECK();
-      std::swap(V, U);
     }
   }
+  // Ritz vectors of the converged (or last) iteration's basis, into W
+  if (ctl)
+    split_apply_kernel<T><<<nblk, 256, 0, st>>>(Vb[0], S, M, b, W, ctl, 1, Vb[1]);
+  else
+    split_apply_kernel<T><<<nblk, 256, 0, st>>>(Vb[(iters - 1) & 1], S, M, b, W);
+  MACH_LAUNCH_CHECK();
   if (a.basis_out) {
     copy_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024), 256, 0, st>>>(
-        U, a.basis_out, (int64_t)M * b);
+        W, a.basis_out, (int64_t)M * b);
     MACH_LAUNCH_CHECK();
   }
-  split_vout_kernel<T><<<(unsigned)ceil_div(M, 128), 128, 0, st>>>(U, M, b, e.r, e.rr, a.Vout, a.theta, a.stats,
-                                                                   iters);
+  split_finish_kernel<<<1, 32, 0, st>>>(e.r, e.rr, a.theta, a.stats, iters, ctl);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
 
+template <typename T>
+EigResult<T> eig_result(const EigLaunch& e) {
+  EigResult<T> out;
+  if (e.M <= kEigSmallMax) {
+    out.U = eig_out_u<T>(e.Vout, e.r);
+    out.ldu = e.r;
+    out.X = e.Vout;
+  } else {
+    out.U = static_cast<const T*>(e.W);   // the Ritz vectors of the split path
+    out.ldu = e.b;
+    out.X = e.rr;
+  }
+  out.theta = e.theta;
+  return out;
+}
+
+size_t eig_out_bytes(int M) { return (size_t)kMaxRank * kMaxRank * sizeof(double) + (size_t)M * kMaxRank * 8; }
+
+template EigResult<float> eig_result<float>(const EigLaunch&);
+template EigResult<double> eig_result<double>(const EigLaunch&);
 template mach_status launch_eig<float>(const float*, const EigLaunch&, cudaStream_t);
 template mach_status launch_eig<double>(const double*, const EigLaunch&, cudaStream_t);
 

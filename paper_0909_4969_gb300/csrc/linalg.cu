@@ -171,9 +171,12 @@ __global__ void copy_cols(const T* __restrict__ A, int M, int r, T* V, int b) {
 }
 
 // ----------------------------------------------------------------------------
-// Factor from eigenvectors:
-//  J-route: A64[i][k] = sum_j Y[i][j] Vout[j][k] / sqrt(theta_k)   (FP64)
-//  I-route: A64 = Vout.
+// Factor from eigenvectors.  The eigensolver returns its leading Ritz basis
+// U_r (M x r, T, leading dimension ldu) and the FP64 rotation X (r x r) that
+// the final Rayleigh-Ritz refinement applied to it; the eigenvectors are
+// U_r X, formed here (FP64 work spread over the CTAs):
+//  J-route: A64[i][k] = sum_m (sum_j Y[i][j] U_r[j][m]) X[m][k] / sqrt(theta_k)
+//  I-route: A64[i][k] = sum_m U_r[i][m] X[m][k].
 // Then FP64 Cholesky QR: every CTA writes its partial Gram A_blk^T A_blk to
 // part[blockIdx] (register accumulation per lane, warp partials reduced in
 // shared memory); the last CTA to finish sums the partials in block order
@@ -183,20 +186,26 @@ constexpr int kPairsPerLane = (kMaxRank * kMaxRank + 31) / 32;
 constexpr size_t kLsvStageBytes = 48 * 1024;
 
 template <typename T>
-__global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y, const double* __restrict__ Vout,
+__global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y, const T* __restrict__ U, int ldu,
+                                                        const double* __restrict__ X,
                                                         const double* __restrict__ theta, int I, int J, int r,
                                                         int jroute, double* __restrict__ A64, double* part,
                                                         unsigned* counter, double* rinv, unsigned* err) {
   __shared__ double wsum[8][kMaxRank * kMaxRank];
   __shared__ double sinv[kMaxRank];
+  __shared__ double Xs[kMaxRank * kMaxRank];
   __shared__ bool last;
-  // the row products Y V run in the arithmetic of Y (T); V is staged in
-  // shared memory in T when it fits
+  // the row products Y U_r run in the arithmetic of Y (T); U_r is staged in
+  // shared memory when it fits
   extern __shared__ __align__(16) unsigned char lsv_smem[];
-  T* Vs = reinterpret_cast<T*>(lsv_smem);
+  T* Us = reinterpret_cast<T*>(lsv_smem);
   const bool staged = jroute && (size_t)J * r * sizeof(T) <= kLsvStageBytes;
   if (staged)
-    for (int e = threadIdx.x; e < J * r; e += blockDim.x) Vs[e] = (T)Vout[e];
+    for (int e = threadIdx.x; e < J * r; e += blockDim.x) {
+      const int j = e / r, m = e - (e / r) * r;
+      Us[e] = U[(size_t)j * ldu + m];
+    }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Xs[e] = X[e];
   if (threadIdx.x < r) sinv[threadIdx.x] = theta[threadIdx.x] > 0.0 ? 1.0 / sqrt(theta[threadIdx.x]) : 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -205,7 +214,7 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
 #pragma unroll
   for (int k = 0; k < kPairsPerLane; ++k) gacc[k] = 0.0;
   for (int i = blockIdx.x * nw + warp; i < I; i += gridDim.x * nw) {
-    double arow[kMaxRank];
+    double u[kMaxRank];
     if (jroute) {
       T sacc[kMaxRank];
 #pragma unroll
@@ -215,19 +224,31 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
         if (staged) {
 #pragma unroll
           for (int k = 0; k < kMaxRank; ++k)
-            if (k < r) sacc[k] += y * Vs[j * r + k];
+            if (k < r) sacc[k] += y * Us[j * r + k];
         } else {
 #pragma unroll
           for (int k = 0; k < kMaxRank; ++k)
-            if (k < r) sacc[k] += y * (T)Vout[(size_t)j * r + k];
+            if (k < r) sacc[k] += y * U[(size_t)j * ldu + k];
         }
       }
 #pragma unroll
-      for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? (double)warp_sum(sacc[k]) * sinv[k] : 0.0;
+      for (int k = 0; k < kMaxRank; ++k) u[k] = k < r ? (double)warp_sum(sacc[k]) : 0.0;
     } else {
 #pragma unroll
-      for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? Vout[(size_t)i * r + k] : 0.0;
+      for (int k = 0; k < kMaxRank; ++k) u[k] = k < r ? (double)U[(size_t)i * ldu + k] : 0.0;
     }
+    // lane k forms entry k of the row (r FP64 products), then every lane
+    // takes the whole row by shuffles for the Gram pairs
+    double mine = 0.0;
+    if (lane < r) {
+#pragma unroll
+      for (int m = 0; m < kMaxRank; ++m)
+        if (m < r) mine += u[m] * Xs[m * r + lane];
+      if (jroute) mine *= sinv[lane];
+    }
+    double arow[kMaxRank];
+#pragma unroll
+    for (int k = 0; k < kMaxRank; ++k) arow[k] = k < r ? __shfl_sync(0xffffffffu, mine, k) : 0.0;
     if (lane < r) A64[(size_t)i * r + lane] = arow[lane < kMaxRank ? lane : 0];
 #pragma unroll
     for (int k = 0; k < kPairsPerLane; ++k) {
@@ -401,16 +422,16 @@ mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, 
 }
 
 template <typename T>
-mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* theta, int I, int J, int r, bool jroute,
-                              double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
-                              double* out_colmajor, T* out_rowmajor, cudaStream_t st) {
+mach_status launch_lsv_finish(const T* Y, const EigResult<T>& ev, int I, int J, int r, bool jroute, double* A64,
+                              double* gram64, unsigned* counter, double* rinv, unsigned* err, double* out_colmajor,
+                              T* out_rowmajor, cudaStream_t st) {
   MACH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   // few partial Grams for the last CTA to sum: at most 64 CTAs, several rows per warp
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 32), 64));
   const size_t vbytes = (size_t)J * r * sizeof(T);
   const size_t smem = jroute && vbytes <= kLsvStageBytes ? vbytes : 0;
-  lsv_apply_kernel<T><<<blocks, 256, smem, st>>>(Y, Vout, theta, I, J, r, jroute ? 1 : 0, A64, gram64, counter,
-                                                  rinv, err);
+  lsv_apply_kernel<T><<<blocks, 256, smem, st>>>(Y, ev.U, ev.ldu, ev.X, ev.theta, I, J, r, jroute ? 1 : 0, A64,
+                                                  gram64, counter, rinv, err);
   MACH_LAUNCH_CHECK();
   lsv_finish_kernel<T><<<(unsigned)ceil_div((int64_t)I * r, 256), 256, 0, st>>>(A64, rinv, I, r, out_colmajor,
                                                                                  out_rowmajor);
@@ -438,9 +459,8 @@ mach_status launch_core(const T* Y, const double* A, int I, int J, int r, double
   template mach_status launch_gram<T>(const T*, int64_t, int, int64_t, int64_t, T*, T*, int64_t, cudaStream_t);  \
   template mach_status launch_start_block<T>(const T*, const T*, int, int, int, int, bool, bool, T*, T*,       \
                                              uint32_t, cudaStream_t);                                            \
-  template mach_status launch_lsv_finish<T>(const T*, const double*, const double*, int, int, int, bool,         \
-                                            double*, double*, unsigned*, double*, unsigned*, double*, T*,        \
-                                            cudaStream_t);                                                       \
+  template mach_status launch_lsv_finish<T>(const T*, const EigResult<T>&, int, int, int, bool, double*,        \
+                                            double*, unsigned*, double*, unsigned*, double*, T*, cudaStream_t);  \
   template mach_status launch_factor_to_rowmajor<T>(const double*, int, int, T*, cudaStream_t);                  \
   template mach_status launch_core<T>(const T*, const double*, int, int, int, double, double*, cudaStream_t);
 MACH_INST(float)

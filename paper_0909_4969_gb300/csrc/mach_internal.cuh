@@ -246,8 +246,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait on an mbarrier phase; returns false (and the caller flags
 // DEV_TIMEOUT) when the limit is reached.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
+  for (long long it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     __nanosleep(64);
   }
@@ -308,7 +308,29 @@ struct DevBuf {
 mach_status dev_alloc(DevBuf& b, size_t bytes, cudaStream_t s);
 void dev_free(DevBuf& b, cudaStream_t s);
 
+// A DevBuf released (stream-ordered) when it goes out of scope, so that
+// every early return of a host routine frees its temporaries.
+struct ScopedDevBuf : DevBuf {
+  cudaStream_t st;
+  explicit ScopedDevBuf(cudaStream_t s) : st(s) {}
+  ~ScopedDevBuf() { dev_free(*this, st); }
+  ScopedDevBuf(const ScopedDevBuf&) = delete;
+  ScopedDevBuf& operator=(const ScopedDevBuf&) = delete;
+};
+
 int num_sms();
+
+// HOSVD Gram X^_(n) X^_(n)^T on the tensor cores (tcgram.cu), from the
+// fibres along mode n; terms = 1 (BF16 values) or 2 (BF16 pair, about 16
+// significant bits).  scratch: tc_gram_scratch_bytes(I) bytes.
+int tc_gram_max_order();
+size_t tc_gram_scratch_bytes(int I);
+template <typename T>
+mach_status launch_tc_gram(const void* val, mach_dtype vdt, const uint16_t* leaf, const uint32_t* fib_start,
+                           int64_t nfib, int I, int terms, float* scratch, T* C, unsigned* err, cudaStream_t st);
+
+// Self-check of the bounded mbarrier wait (selfcheck.cu).
+mach_status run_bounded_wait_check(long long limit, int arrive, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // Kernel launchers (one definition each, in sample.cu / sort.cu / ttmc.cu /
@@ -472,17 +494,32 @@ struct EigLaunch {
   void* part;                  // >= eig_part_elems(M) elements of T (split path)
   unsigned long long* stats;   // device counters: calls, iterations, unconverged
   void* basis_out;             // M x b T: final Ritz block, or null
-  double* rr;                  // >= kMaxRank * (kMaxRank + 1) doubles (split path)
+  double* rr;                  // >= kMaxRank * (kMaxRank + 1) doubles (split path); may alias Vout
+  unsigned long long* ctl = nullptr;   // 3 device words: the FP32 split path's convergence test and early exit
 };
 int eig_split_threshold();
 size_t eig_part_elems(int M);
 template <typename T>
 mach_status launch_eig(const T* C, const EigLaunch& e, cudaStream_t st);
+// Where a finished launch_eig left its result: the leading Ritz basis U_r
+// (M x r, T, leading dimension ldu), the FP64 rotation X (r x r row-major)
+// with U_r X = the eigenvectors, and theta (r eigenvalues, descending).
+template <typename T>
+struct EigResult {
+  const T* U;
+  int ldu;
+  const double* X;
+  const double* theta;
+};
+template <typename T>
+EigResult<T> eig_result(const EigLaunch& e);
+// Bytes of the output area e.Vout for orders up to M.
+size_t eig_out_bytes(int M);
 template <typename T>
 mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
                                T* V, T* scratch, uint32_t salt, cudaStream_t st);
 template <typename T>
-mach_status launch_lsv_finish(const T* Y, const double* Vout, const double* theta, int I, int J, int r, bool jroute,
+mach_status launch_lsv_finish(const T* Y, const EigResult<T>& ev, int I, int J, int r, bool jroute,
                               double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,
                               double* out_colmajor, T* out_rowmajor, cudaStream_t st);
 template <typename T>

@@ -354,6 +354,194 @@ __global__ void __launch_bounds__(32 * TtmcWarps<T>::value) ttmc_kernel(TtmcArgs
   if (cur_row >= 0) flush_row();
 }
 
+// The 3-way chain with the fold kept in registers: lane j owns fibre j of a
+// batch of 32, forms z_f (leaf level, as above), reads the mid factor row
+// of the fibre and adds the outer product A_mid[i_mid(f), :] (x) z_f to its
+// own copy of the row's RM x RL accumulators.  The 32 copies are summed once
+// per (warp, row) run, in lane order, through a shared-memory transpose.
+// Compared with the shared-memory fold above this reads no z vectors back
+// from shared memory (about a third of the shared-memory loads per fibre);
+// it holds RM * RL accumulators per lane, so it serves FP32 arithmetic and
+// RM * RL <= 100.
+template <typename V, int RM, int RL, int KW>
+__global__ void __launch_bounds__(32 * KW, 1) ttmc3_kernel(TtmcArgs<float> a) {
+  using T = float;
+  constexpr int J = RM * RL;
+  constexpr int NC = (J + 31) / 32;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar_fac;
+  __shared__ uint64_t bar_warp[KW][2];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const V* val = static_cast<const V*>(a.val);
+  const uint32_t fac_bytes = a.leaf_bytes_staged + a.mid0_bytes_staged;
+  unsigned char* wbuf0 = smem_raw + fac_bytes + (size_t)warp * 2 * WarpStage<V>::kBytes;
+  float* red = reinterpret_cast<float*>(smem_raw + fac_bytes + (size_t)KW * 2 * WarpStage<V>::kBytes) +
+               (size_t)warp * 32 * 33;
+
+  if (tid == 0) {
+    mbar_init(&bar_fac, 1);
+    for (int w = 0; w < KW; ++w) {
+      mbar_init(&bar_warp[w][0], 1);
+      mbar_init(&bar_warp[w][1], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const T* Aleaf = a.A_leaf;
+  const T* Amid = a.A_mid0;
+  if (fac_bytes) {
+    T* sLeaf = reinterpret_cast<T*>(smem_raw);
+    T* sMid = reinterpret_cast<T*>(smem_raw + a.leaf_bytes_staged);
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bar_fac, fac_bytes);
+      if (a.leaf_bytes_staged) bulk_g2s(sLeaf, a.A_leaf, a.leaf_bytes_staged, &bar_fac);
+      if (a.mid0_bytes_staged) bulk_g2s(sMid, a.A_mid0, a.mid0_bytes_staged, &bar_fac);
+    }
+    if (!mbar_wait_bounded(&bar_fac, 0)) {
+      if (tid == 0) atomicOr(a.err, DEV_TIMEOUT);
+      return;
+    }
+    if (a.leaf_bytes_staged) Aleaf = sLeaf;
+    if (a.mid0_bytes_staged) Amid = sMid;
+  }
+
+  const uint32_t ntask = *a.d_ntask;
+  const uint32_t nfib = *a.d_nfib;
+  const int gwarp = blockIdx.x * KW + warp;
+  const int nwarps = gridDim.x * KW;
+  uint32_t phase_bits = 0;
+  constexpr uint32_t kAlign = 16 / sizeof(uint16_t);
+  auto stage_task = [&](uint32_t tt, int buf) {
+    if (lane == 0) {
+      const int4 tk = a.tasks[tt];
+      const uint32_t b0 = (uint32_t)tk.y & ~(kAlign - 1);
+      const uint32_t ns = (((uint32_t)tk.z - b0) + kAlign - 1) & ~(kAlign - 1);
+      const uint32_t vb = ns * (uint32_t)sizeof(V), lb = ns * 2u;
+      unsigned char* wb = wbuf0 + (size_t)buf * WarpStage<V>::kBytes;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar_warp[warp][buf], vb + lb);
+      bulk_g2s(wb, val + b0, vb, &bar_warp[warp][buf]);
+      bulk_g2s(wb + WarpStage<V>::kValBytes, a.leaf + b0, lb, &bar_warp[warp][buf]);
+    }
+  };
+  const uint32_t per = (ntask + (uint32_t)nwarps - 1u) / (uint32_t)nwarps;
+  const uint32_t tb = min(ntask, (uint32_t)gwarp * per), te = min(ntask, tb + per);
+  if (tb < te) stage_task(tb, 0);
+  int cur = 0;
+  T acc[J];
+#pragma unroll
+  for (int q = 0; q < J; ++q) acc[q] = T(0);
+  int cur_row = -1;
+  uint32_t head = 0;
+
+  auto flush_row = [&]() {
+    const uint32_t rt0 = a.row_task[cur_row], rt1 = a.row_task[cur_row + 1];
+    const bool whole = rt0 >= tb && rt1 <= te;
+    T* dst = whole ? a.Y + (size_t)cur_row * a.J : a.partial + (size_t)head * a.J;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (32 * c + j < J) red[lane * 33 + j] = acc[32 * c + j];
+      __syncwarp();
+      if (32 * c + lane < J) {
+        T sum = T(0);
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) sum += red[l * 33 + lane];
+        dst[32 * c + lane] = sum;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < J; ++q) acc[q] = T(0);
+  };
+
+  for (uint32_t t = tb; t < te; ++t, cur ^= 1) {
+    if (t + 1 < te) stage_task(t + 1, cur ^ 1);
+    const int4 tk = a.tasks[t];
+    const int row = tk.x;
+    const uint32_t e0 = (uint32_t)tk.y, e1 = (uint32_t)tk.z;
+    const uint32_t base = e0 & ~(kAlign - 1);
+    unsigned char* wbuf = wbuf0 + (size_t)cur * WarpStage<V>::kBytes;
+    const V* sval = reinterpret_cast<const V*>(wbuf);
+    const uint16_t* sleaf = reinterpret_cast<const uint16_t*>(wbuf + WarpStage<V>::kValBytes);
+    if (row != cur_row) {
+      if (cur_row >= 0) flush_row();
+      cur_row = row;
+      head = t;
+    }
+    if (!mbar_wait_bounded(&bar_warp[warp][cur], (phase_bits >> cur) & 1u)) {
+      if (lane == 0) atomicOr(a.err, DEV_TIMEOUT);
+      if (t + 1 < te) (void)mbar_wait_bounded(&bar_warp[warp][cur ^ 1], (phase_bits >> (cur ^ 1)) & 1u);
+      return;
+    }
+    phase_bits ^= 1u << cur;
+    uint32_t fs_n, mid_n, fl_n = 0;
+    {
+      const uint32_t f = (uint32_t)tk.w + lane;
+      fs_n = f < nfib ? a.fib_start[f] : 0xffffffffu;
+      mid_n = f < nfib ? a.fib_mid[f] : 0u;
+      if (lane == 31 && f + 1 <= nfib) fl_n = a.fib_start[f + 1];
+    }
+    for (uint32_t fb = (uint32_t)tk.w;; fb += 32) {
+      const uint32_t f = fb + lane;
+      const uint32_t fs = fs_n, mid_f = mid_n;
+      uint32_t fe = __shfl_down_sync(0xffffffffu, fs, 1);
+      if (lane == 31) fe = fl_n;
+      const bool valid = f < nfib && fs < e1;
+      if (!__ballot_sync(0xffffffffu, valid)) break;
+      {
+        const uint32_t fn = f + 32;
+        fs_n = fn < nfib ? a.fib_start[fn] : 0xffffffffu;
+        mid_n = fn < nfib ? a.fib_mid[fn] : 0u;
+        if (lane == 31 && fn + 1 <= nfib) fl_n = a.fib_start[fn + 1];
+      }
+      if (valid) {
+        T z[RL];
+#pragma unroll
+        for (int b = 0; b < RL; ++b) z[b] = T(0);
+        const uint32_t s0 = (fs > e0 ? fs : e0) - base;
+        const uint32_t s1 = (fe < e1 ? fe : e1) - base;
+        for (uint32_t e = s0; e < s1; ++e) {
+          const T v = (T)sval[e];
+          const T* ar = Aleaf + (size_t)sleaf[e] * RL;
+          if ((RL % 2) == 0) {
+#pragma unroll
+            for (int b = 0; b < RL / 2; ++b) {
+              const float2 w2 = reinterpret_cast<const float2*>(ar)[b];
+              z[2 * b] += v * w2.x;
+              z[2 * b + 1] += v * w2.y;
+            }
+          } else {
+#pragma unroll
+            for (int b = 0; b < RL; ++b) z[b] += v * ar[b];
+          }
+        }
+        T m[RM];
+        const T* mr = Amid + (size_t)mid_f * RM;
+        if ((RM % 2) == 0) {
+#pragma unroll
+          for (int i = 0; i < RM / 2; ++i) {
+            const float2 w2 = reinterpret_cast<const float2*>(mr)[i];
+            m[2 * i] = w2.x;
+            m[2 * i + 1] = w2.y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RM; ++i) m[i] = mr[i];
+        }
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int b = 0; b < RL; ++b) acc[i * RL + b] += m[i] * z[b];
+      }
+    }
+    __syncwarp();   // the staging buffer is reused by the next task
+  }
+  if (cur_row >= 0) flush_row();
+}
+
 // Rows split over several warps' task blocks: Y_row = sum of the partials of
 // the runs, i.e. of the row's first task and of every later task that starts
 // a warp block (t a multiple of `per`), in increasing task order.  Rows that
@@ -438,6 +626,84 @@ static mach_status launch_ttmc_t(const TtmcLaunch& L, cudaStream_t st) {
   return MACH_OK;
 }
 
+// The register-fold 3-way chain (ttmc3_kernel) for FP32 arithmetic and the
+// (r_mid, r_leaf) pairs instantiated here; false when it does not apply.
+template <typename V, int RM, int RL>
+static mach_status launch_ttmc3_t(const TtmcLaunch& L, cudaStream_t st) {
+  constexpr int KW = RM * RL > 64 ? 12 : 16;
+  TtmcArgs<float> a;
+  a.val = L.val;
+  a.leaf = L.leaf;
+  a.fib_start = L.fib_start;
+  a.fib_mid = L.fib_mid;
+  a.tasks = L.tasks;
+  a.d_ntask = L.d_ntask;
+  a.d_nfib = L.d_nfib;
+  a.row_task = L.row_task;
+  a.A_leaf = static_cast<const float*>(L.A_leaf);
+  a.A_mid0 = static_cast<const float*>(L.A_mid0);
+  a.A_mid1 = nullptr;
+  a.r_leaf = L.r_leaf;
+  a.r_mid0 = L.r_mid0;
+  a.r_mid1 = 1;
+  a.J = L.J;
+  a.Q = L.J;
+  a.Y = static_cast<float*>(L.Y);
+  a.partial = static_cast<float*>(L.partial);
+  a.err = L.err;
+  auto kern = ttmc3_kernel<V, RM, RL, KW>;
+  cudaFuncAttributes fa;
+  MACH_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, optin = 0;
+  MACH_CUDA_TRY(cudaGetDevice(&dev));
+  MACH_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t fixed = (size_t)KW * 2 * WarpStage<V>::kBytes + (size_t)KW * 32 * 33 * sizeof(float);
+  size_t budget = (size_t)optin > fa.sharedSizeBytes + fixed + 1024 ? (size_t)optin - fa.sharedSizeBytes - fixed - 1024
+                                                                    : 0;
+  auto take = [&](size_t elems) -> uint32_t {
+    const size_t by = (elems * sizeof(float) + 15) & ~(size_t)15;
+    if (elems == 0 || by > budget) return 0u;
+    budget -= by;
+    return (uint32_t)by;
+  };
+  a.leaf_bytes_staged = take((size_t)L.I_leaf * L.r_leaf);
+  a.mid0_bytes_staged = take((size_t)L.I_mid0 * L.r_mid0);
+  a.mid1_bytes_staged = 0;
+  const size_t smem = (size_t)a.leaf_bytes_staged + a.mid0_bytes_staged + fixed;
+  MACH_TRY(allow_max_dyn_smem(kern));
+  int per_sm = 0;
+  MACH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * KW, smem));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  const int64_t need = ceil_div(L.ntask_cap, KW);
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, 32 * KW, smem, st>>>(a);
+  MACH_LAUNCH_CHECK();
+  ttmc_fixup_kernel<float><<<L.nrows, 128, 0, st>>>(L.row_task, L.d_ntask, (uint32_t)(grid * KW), L.J,
+                                                     static_cast<const float*>(L.partial), static_cast<float*>(L.Y));
+  MACH_LAUNCH_CHECK();
+  return MACH_OK;
+}
+
+template <typename V>
+static bool launch_ttmc3(const TtmcLaunch& L, cudaStream_t st, mach_status* s) {
+  const int rm = L.r_mid0, rl = L.r_leaf;
+#define MACH_TTMC3(RM_, RL_)                          \
+  if (rm == RM_ && rl == RL_) {                       \
+    *s = launch_ttmc3_t<V, RM_, RL_>(L, st);          \
+    return true;                                      \
+  }
+  MACH_TTMC3(10, 10)
+  MACH_TTMC3(4, 8)
+  MACH_TTMC3(8, 4)
+  MACH_TTMC3(4, 4)
+  MACH_TTMC3(8, 8)
+  MACH_TTMC3(5, 5)
+#undef MACH_TTMC3
+  return false;
+}
+
 template <typename V, typename T, int D, int ACC>
 static mach_status launch_ttmc_rl(const TtmcLaunch& L, cudaStream_t st) {
   // leaf-rank widths: exact for the common ranks 4, 5, 8, 10, padded otherwise
@@ -484,11 +750,14 @@ mach_status launch_to_bf16(const void* val, mach_dtype dt, int64_t K, void* out,
 }
 
 mach_status launch_ttmc(const TtmcLaunch& L, bool compute_fp64, cudaStream_t st) {
+  mach_status s = MACH_OK;
   if (L.bf16) {
     if (compute_fp64) return MACH_EINVAL;
+    if (L.d == 3 && launch_ttmc3<__nv_bfloat16>(L, st, &s)) return s;
     return launch_ttmc_vt<__nv_bfloat16, float>(L, st);
   }
   if (L.vdt == MACH_F32) {
+    if (!compute_fp64 && L.d == 3 && launch_ttmc3<float>(L, st, &s)) return s;
     return compute_fp64 ? launch_ttmc_vt<float, double>(L, st) : launch_ttmc_vt<float, float>(L, st);
   }
   return compute_fp64 ? launch_ttmc_vt<double, double>(L, st) : launch_ttmc_vt<double, float>(L, st);

@@ -45,6 +45,8 @@ SIGNATURES = {
     "mach_sample_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "mach_sample_fibers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i64p]),
     "mach_sample_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "mach_sample_gram": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "mach_sample_stats": (ctypes.c_int, [ctypes.c_void_p, _c_i64p, _c_i64p, _c_i64p,
                                          ctypes.POINTER(ctypes.c_uint)]),
     "mach_hooi": (ctypes.c_int, [ctypes.c_void_p, _c_intp, ctypes.c_int, ctypes.c_int, _c_pp, ctypes.c_void_p,
@@ -69,6 +71,7 @@ SIGNATURES = {
     "mach_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mach_profile_query": (ctypes.c_int, [ctypes.c_int, _c_dblp, _c_i64p, _c_dblp]),
     "mach_launch_count": (ctypes.c_int64, []),
+    "mach_check_bounded_wait": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -239,6 +242,16 @@ class Sample:
                                                                 1 if warm else 0, _stream(stream)))
         return G, factors
 
+    def gram(self, mode: int, method: int = 0, stream=None) -> torch.Tensor:
+        """mach_sample_gram: X^_(n) X^_(n)^T (raw values) as an FP64 I_n x I_n
+        device tensor; method 0 exact FP64, 1 / 2 tensor cores (1 / 2 BF16
+        terms)."""
+        n = self.dims[mode] if 0 <= mode < self.d else 1   # the library rejects a bad mode
+        out = torch.empty((n, n), dtype=torch.float64, device=self.device)
+        _check("mach_sample_gram", self._lib.mach_sample_gram(self.handle, int(mode), int(method),
+                                                              ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
     def core(self, ranks: Sequence[int], factors: Sequence[torch.Tensor], stream=None) -> torch.Tensor:
         factors = [colmajor(f) if f.stride(0) != 1 else f for f in factors]
         G = torch.empty(tuple(int(r) for r in ranks), dtype=torch.float64, device=self.device)
@@ -405,6 +418,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def check_bounded_wait(limit: int, arrive: bool, stream=None) -> int:
+    """mach_check_bounded_wait: returns the status code (0 = the wait
+    completed, 5 = MACH_ETIMEOUT: it ran out of polls and returned)."""
+    return int(load().mach_check_bounded_wait(int(limit), 1 if arrive else 0, _stream(stream)))
 
 
 def version() -> str:

@@ -69,12 +69,14 @@ def compare_decomposition(O, X, G_o, A_o, G_g, A_g, tol, label="", rounding=None
         assert dist <= tol, "%s mode %d subspace distance %.3e > %.1e" % (label, k, dist, tol)
         ortho = np.max(np.abs(A_g[k].T @ A_g[k] - np.eye(A_g[k].shape[1])))
         assert ortho <= max(tol, 1e-12), "%s mode %d not orthonormal: %.3e" % (label, k, ortho)
-    if rounding is None or rounding / max(min_core_gap(G_o), 1e-300) <= tol:
-        Go = sign_fixed_core(G_o, A_o)
-        Gg = sign_fixed_core(G_g, A_g)
-        rel = np.linalg.norm(Go - Gg) / np.linalg.norm(Go)
+    gap = min_core_gap(G_o)
+    core_compared = rounding is None or rounding / max(gap, 1e-300) <= tol
+    Go = sign_fixed_core(G_o, A_o)
+    Gg = sign_fixed_core(G_g, A_g)
+    rel = float(np.linalg.norm(Go - Gg) / np.linalg.norm(Go))
+    if core_compared:
         assert rel <= tol, "%s core relative difference %.3e > %.1e" % (label, rel, tol)
     eo = O.relative_error(X, G_o, A_o)
     eg = O.relative_error(X, G_g, A_g)
     assert abs(eo - eg) <= tol * max(1.0, eo), "%s reconstruction error %.12f vs %.12f" % (label, eg, eo)
-    return eo, eg
+    return {"eo": eo, "eg": eg, "core_compared": bool(core_compared), "core_rel": rel, "core_gap": gap}

@@ -46,3 +46,6 @@ def test_host_only_calls():
     assert lib.mach_sample(ctypes.c_void_p(17), 0, 3, dims, 0.5, 1, None, ctypes.byref(h)) == 1
     n = ctypes.c_int64()
     assert lib.mach_sample_count(None, ctypes.byref(n)) == 1
+    # the bounded-wait self-check validates its poll limit before device work
+    assert lib.mach_check_bounded_wait(0, 0, None) == 1
+    assert lib.mach_check_bounded_wait((1 << 23) + 1, 1, None) == 1

@@ -1,0 +1,155 @@
+"""GPU parity at the shapes the benchmark workloads run, against the FP64
+oracle: the single large decomposition at full size (1000^3 FP32, p = 0.01,
+ranks 10, 20 sweeps) in both sweep arithmetics, a subset of the 512 uneven
+batched windows drawn with the workload's own size ranges, a cold resized
+served window (1000 x 32 x 4096), and the 4-way mixed-precision workload at
+100^4 (its kernels' full-size routes).  Tolerances: 1e-10 for FP64 sweeps,
+1e-5 for FP32 and BF16 + refinement (subspace distance, sign-fixed core,
+Section 4's reconstruction error)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mach_oracle as O
+from paper_0909_4969_gb300 import synth
+from tests._gpu import compare_decomposition, mach_module, min_core_gap, sign_fixed_core, torch
+from tests._oracle_pool import oracle_hooi_many
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def _core_rel(G_a, A_a, G_b, A_b):
+    Ga, Gb = sign_fixed_core(G_a, A_a), sign_fixed_core(G_b, A_b)
+    return float(np.linalg.norm(Ga - Gb) / np.linalg.norm(Gb))
+
+
+def test_large_workload_full_size():
+    """1000 x 1000 x 1000 FP32 (4 GB), rank-(10,10,10) Gaussian core, 5%
+    noise, p = 0.01 (~1e7 kept), 20 sweeps: the sampled set is the oracle's,
+    the FP64 sweeps match the oracle within 1e-10 and the FP32 sweeps match
+    the oracle and the FP64 sweeps within 1e-5."""
+    mach = mach_module()
+    w = synth.config_large_fp32(1000)
+    ranks = w.spec.ranks
+    X, _, _ = synth.tucker_torch(w.spec, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = mach.sample(X, w.p, w.spec.seed)
+        idx = s.indices().cpu().numpy()
+        G32, A32 = s.hooi(ranks, w.sweeps, "fp32")
+        G64, A64 = s.hooi(ranks, w.sweeps, "fp64")
+        st.synchronize()
+        assert s.stats()["flags"] == 0
+        s.free()
+    Xh = X.cpu().numpy()
+    del X
+    torch.cuda.empty_cache()
+    S, G_o, A_o = O.mach_hooi(Xh, ranks, w.p, w.spec.seed, w.sweeps)
+    assert np.array_equal(idx, S.idx), "sampled index set differs from the oracle"
+    dec = {"fp32": (G32.cpu().numpy(), [a.cpu().numpy() for a in A32]),
+           "fp64": (G64.cpu().numpy(), [a.cpu().numpy() for a in A64])}
+    e_o = O.relative_error(Xh, G_o, A_o, slab=50)
+    errs = {k: O.relative_error(Xh, G, A, slab=50) for k, (G, A) in dec.items()}
+    # every comparison is computed and reported before any is asserted
+    (G3, A3), (G6, A6) = dec["fp32"], dec["fp64"]
+    rows = []
+    for prec, (G, A) in dec.items():
+        rows.append((prec + " vs oracle", TOL[prec], [O.subspace_distance(A_o[k], A[k]) for k in range(3)],
+                     _core_rel(G, A, G_o, A_o), abs(errs[prec] - e_o)))
+    rows.append(("fp32 vs fp64", TOL["fp32"], [O.subspace_distance(A6[k], A3[k]) for k in range(3)],
+                 _core_rel(G3, A3, G6, A6), abs(errs["fp32"] - errs["fp64"])))
+    report = "; ".join("%s: subspace %s core %.2e error %.2e" % (name, ["%.2e" % v for v in d], c, e)
+                       for name, _, d, c, e in rows)
+    print(report)
+    for name, tol, d, c, e in rows:
+        assert max(d) <= tol and c <= tol and e <= tol * max(1.0, e_o), report
+
+
+# The 1e-5 bound of the FP32 forms is stated for subspaces and reconstruction
+# error, which are compared for every item; the sign-fixed core also needs
+# the individual singular vectors, which FP32 arithmetic fixes to about
+# u / gap (u = 2^-24, with a constant measured below 2.5), so the core is
+# compared where 4u / gap <= 1e-5 (every core singular-value gap at least
+# 2.4e-2; the count of such items is asserted, so that the comparison is
+# not vacuous).
+U32 = 2.0 ** -22
+
+
+def test_batched_workload_shapes():
+    """16 of the 512 uneven windows of the batched workload (every 32nd:
+    hosts 50-400, types 8-32, timeticks 64-2048), p = 0.1, ranks (4, 4, 8),
+    10 sweeps, through one mach_hooi_batched launch."""
+    mach = mach_module()
+    ws = synth.config_batched(512)[::32]
+    ranks, p, sweeps = (4, 4, 8), 0.1, 10
+    Xs = [synth.tucker_numpy(w.spec)[0] for w in ws]
+    seeds = [int(w.name.split("_")[1]) for w in ws]
+    ref = oracle_hooi_many([(X, ranks, p, sd, sweeps) for X, sd in zip(Xs, seeds)])
+    samples = [mach.sample(torch.from_numpy(np.ascontiguousarray(X)).cuda(), p, sd) for X, sd in zip(Xs, seeds)]
+    cores, facs = mach.hooi_batched(samples, ranks, sweeps)
+    torch.cuda.synchronize()
+    compared = 0
+    for b, (X, s) in enumerate(zip(Xs, samples)):
+        assert s.stats()["flags"] == 0
+        idx, G_o, A_o = ref[b]
+        assert np.array_equal(s.indices().cpu().numpy(), idx)
+        r = compare_decomposition(O, X.astype(np.float64), G_o, A_o, cores[b].cpu().numpy(),
+                                  [a.cpu().numpy() for a in facs[b]], TOL["fp32"],
+                                  "batched %s" % (X.shape,), rounding=U32)
+        compared += r["core_compared"]
+        print("  core rel %.2e gap %.2e compared %d" % (r["core_rel"], r["core_gap"], r["core_compared"]))
+        s.free()
+    print("batched workload shapes: core compared on %d of %d" % (compared, len(Xs)))
+    assert compared >= 6, "core compared on only %d of %d items" % (compared, len(Xs))
+
+
+def test_served_resized_window_matches_oracle():
+    """A resized window of the served stream (1000 x 32 x 4096 FP32, rank
+    (4, 4, 8), 5% noise, p = 0.1, 3 sweeps) starts cold from the HOSVD: the
+    server's result matches the oracle's.  Its time mode (I = 4096) takes the
+    multi-CTA eigensolver route of the HOSVD start."""
+    mach = mach_module()
+    ranks, p, sweeps = (4, 4, 8), 0.1, 3
+    X = synth.tucker_for_dims((1000, 32, 4096), ranks, 0.05, 99, "float32")
+    ref = oracle_hooi_many([(X, ranks, p, 7, sweeps)], workers=1)[0]
+    srv = mach.Server(16 << 30, 2)
+    x = torch.from_numpy(X).cuda()
+    t = srv.submit(5, x, ranks, p, 7, sweeps, "fp32")
+    while True:
+        r = srv.poll(t)
+        if r is not None:
+            break
+    srv.close()
+    G_g, A_g, err = r
+    idx, G_o, A_o = ref
+    for k in range(3):
+        assert O.subspace_distance(A_o[k], A_g[k]) <= TOL["fp32"], k
+    if U32 / max(min_core_gap(G_o), 1e-300) <= TOL["fp32"]:
+        assert _core_rel(G_g, A_g, G_o, A_o) <= TOL["fp32"]
+    e_o = O.relative_error(X, G_o, A_o, slab=100)
+    assert abs(err - e_o) <= TOL["fp32"] * max(1.0, e_o), (err, e_o)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_refine"])
+def test_mixed_4way_at_100(prec):
+    """The 4-way workload (log-normal x sign core 8^4, 5% noise, p = 0.05,
+    ranks 8, 10 sweeps) at 100^4: J = 512 > I = 100 in every mode, the same
+    eigensolver route as at 200^4.  BF16_REFINE is compared with the oracle
+    run for its total of 13 sweeps."""
+    mach = mach_module()
+    spec = synth.TuckerSpec((100,) * 4, (8,) * 4, "lognormal_sign", 0.05, 0, "float32")
+    X, _, _ = synth.tucker_numpy(spec)
+    total = 10 + (3 if prec == "bf16_refine" else 0)
+    ref = oracle_hooi_many([(X, spec.ranks, 0.05, 3, total)], workers=1)[0]
+    s = mach.sample(torch.from_numpy(X).cuda(), 0.05, 3)
+    G, A = s.hooi(spec.ranks, 10, prec)
+    torch.cuda.synchronize()
+    assert s.stats()["flags"] == 0
+    idx, G_o, A_o = ref
+    assert np.array_equal(s.indices().cpu().numpy(), idx)
+    s.free()
+    compare_decomposition(O, X.astype(np.float64), G_o, A_o, G.cpu().numpy(), [a.cpu().numpy() for a in A],
+                          TOL["fp32"], "4-way 100^4 %s" % prec)

@@ -197,3 +197,46 @@ def test_tucker2_p_one_matches_brute_force_and_recovers_exact_rank():
             B[n] = O.leading_left_singular_vectors(O.unfold(X, n) @ K, B[n].shape[1])
     for k in (0, 2):
         assert O.subspace_distance(A[k], B[k]) < 1e-12
+
+
+@pytest.mark.parametrize("eps", [1e-3, 0.25, 2.0])
+def test_relative_error_two_spike_closed_form(eps):
+    """Section 4's accuracy measure is the unsquared norm ratio
+    ||X - G x_1 A_1 .. x_d A_d|| / ||X||.  For X = e_111 + eps e_222 and the
+    rank-(1,1,1) model G = [[[1]]], A_k = e_1 the residual is eps e_222, so
+    the measure is eps / sqrt(1 + eps^2) (a squared form would give
+    eps^2 / (1 + eps^2), a residual against X^ or a dropped core term
+    something else).  HOOI at p = 1 finds that model exactly when eps < 1
+    (the larger spike leads every unfolding); with eps > 1 it picks e_2."""
+    X = np.zeros((2, 2, 2))
+    X[0, 0, 0] = 1.0
+    X[1, 1, 1] = eps
+    e1 = np.array([[1.0], [0.0]])
+    want = eps / math.sqrt(1.0 + eps * eps)
+    assert abs(O.relative_error(X, np.ones((1, 1, 1)), [e1, e1, e1]) - want) < 1e-15
+    assert abs(O.relative_error(X, np.ones((1, 1, 1)), [e1, e1, e1], slab=1) - want) < 1e-15
+    S, G, A = O.mach_hooi(X, (1, 1, 1), 1.0, 3, 2)
+    lead = max(1.0, eps)
+    other = min(1.0, eps)
+    assert abs(abs(G.item()) - lead) < 1e-14
+    assert abs(O.relative_error(X, G, A) - other / math.sqrt(1.0 + eps * eps)) < 1e-14
+
+
+def test_relative_error_orthogonal_residual_closed_form():
+    """With orthonormal factors U_k and a residual E orthogonal to
+    span(U_1) (E's mode-1 fibres are projected off U_1), X = G x U + E has
+    ||X - G x U|| = ||E|| and ||X||^2 = ||G||^2 + ||E||^2 (orthonormal
+    products preserve the norm, Section 2.1), so the measure is
+    ||E|| / sqrt(||G||^2 + ||E||^2) exactly; a scale, a square or a
+    transposed factor would break it."""
+    rng = np.random.default_rng(5)
+    dims, ranks = (9, 7, 8), (3, 2, 4)
+    G = rng.standard_normal(ranks)
+    Us = [np.linalg.qr(rng.standard_normal((n, r)))[0] for n, r in zip(dims, ranks)]
+    E = rng.standard_normal(dims)
+    E -= np.einsum("ia,ja,jkl->ikl", Us[0], Us[0], E)      # mode-1 fibres orthogonal to U_1
+    X = np.einsum("abc,ia,jb,kc->ijk", G, *Us) + E
+    nE, nG = np.linalg.norm(E), np.linalg.norm(G)
+    want = nE / math.sqrt(nG ** 2 + nE ** 2)
+    assert abs(O.relative_error(X, G, Us) - want) < 1e-14
+    assert abs(O.relative_error(X, G, Us, slab=4) - want) < 1e-14
