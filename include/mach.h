@@ -364,8 +364,10 @@ mach_status mach_error(const void* x_dev, mach_dtype dtype, int d, const int64_t
  * mach_server_create  budget in bytes (> 0), 1 <= max_slots <= 64, on the
  *                     current device.  *srv receives the server handle.
  * mach_submit         queues one window.  x_dev (device, C order, 16-B
- *                     aligned) stays owned by the caller and must stay valid
- *                     and unchanged until mach_poll reports it done.  Ranks
+ *                     aligned) stays owned by the caller; it must be fully
+ *                     written when mach_submit is called (the server's
+ *                     streams are not ordered after the caller's) and stay
+ *                     valid and unchanged until mach_poll reports it done.  Ranks
  *                     1 <= r_k <= min(I_k, 16).  *ticket identifies the
  *                     request.  Errors: MACH_EINVAL (arguments),
  *                     MACH_ENOMEM_BUDGET (the window can never fit the

@@ -274,7 +274,8 @@ __device__ void bat_lsv(const float* Y, int I, int J, int r, float* A, BatShared
 constexpr int kHosvdB = 16;     // block width of the HOSVD subspace iteration
 constexpr int kHosvdIt = 40;    // its iteration cap (the start of the oracle is the exact HOSVD)
 constexpr int kHosvdCheck = 4;  // Ritz residuals are tested every kHosvdCheck iterations
-constexpr float kHosvdTol = 2e-6f;   // ... against this fraction of the largest Ritz value
+constexpr float kHosvdTol = 5e-7f;   // ... against this fraction of the largest Ritz value, or
+                                     // 10x that once they stop halving (the FP32 floor)
 
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -374,7 +375,8 @@ __device__ void bat_block_rr(const float* Vb, const float* W, int I, int bw, Bat
 // Whether the leading r Ritz pairs of the last bat_block_rr have residuals
 // ||W q_j - theta_j V q_j|| below kHosvdTol theta_1 (all threads return
 // the same answer).
-__device__ bool bat_ritz_converged(const float* Vb, const float* W, int I, int bw, int r, BatShared& sh) {
+__device__ bool bat_ritz_converged(const float* Vb, const float* W, int I, int bw, int r, BatShared& sh,
+                                   float* prev) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float res[kMaxRank];
 #pragma unroll
@@ -415,7 +417,9 @@ __device__ bool bat_ritz_converged(const float* Vb, const float* W, int I, int b
       for (int w = 0; w < kBatWarps; ++w) t += wres[w][k];
       worst = fmaxf(worst, t);
     }
-    conv = th0 > 0.f && sqrtf(worst) <= kHosvdTol * th0 ? 1 : 0;
+    const float rel = th0 > 0.f ? sqrtf(worst) / th0 : 0.f;
+    conv = (th0 > 0.f && rel <= kHosvdTol) || (rel <= 10.f * kHosvdTol && rel > 0.5f * *prev) ? 1 : 0;
+    *prev = rel;
   }
   __syncthreads();
   const bool out = conv != 0;
@@ -444,6 +448,8 @@ __device__ void bat_hosvd_mode(const BatMode& src, int rows_src, int I, int r, u
   __syncthreads();
   if (!exact) bat_orth(Vb, I, bw, kHosvdB, Vb, sh, err);
   bool have_rr = false;
+  __shared__ float prev_res;
+  if (tid == 0) prev_res = 3.0e38f;
   for (int it = 0;; ++it) {
     bat_gram_apply<V>(src, rows_src, I, Vb, W);
     if (exact || it + 1 == kHosvdIt) break;
@@ -451,7 +457,7 @@ __device__ void bat_hosvd_mode(const BatMode& src, int rows_src, int I, int r, u
     // converged (the Rayleigh-Ritz step below is then the one just made)
     if (it % kHosvdCheck == kHosvdCheck - 1) {
       bat_block_rr(Vb, W, I, bw, sh);
-      if (bat_ritz_converged(Vb, W, I, bw, r, sh)) {
+      if (bat_ritz_converged(Vb, W, I, bw, r, sh, &prev_res)) {
         have_rr = true;
         break;
       }

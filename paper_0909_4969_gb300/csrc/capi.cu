@@ -844,16 +844,15 @@ mach_status solve_factor(mach_sample_s* h, Workspace& w, int n, int r, int I, in
   const int M = jroute ? J : I;
   const int b = block_size_for(M, r, !warm, sizeof(T) == 8);
   if (!Y) Y = static_cast<const T*>(w.Y.ptr);
-  MACH_TRY(launch_start_block<T>(Y, static_cast<const T*>(w.fac[n].ptr), I, J, r, b,
-                                 jroute, warm, static_cast<T*>(w.V.ptr), static_cast<T*>(w.ytpart.ptr),
-                                 0x1000u + (uint32_t)n, st));
-  // Columns r..b of the start block: the previous solve's Ritz vectors of the
-  // same Gram shape, when there is one (the next directions after the top r).
-  if (warm && w.basis_M[n] == M && w.basis_b[n] == b && b > r) {
-    MACH_CUDA_TRY(cudaMemcpy2DAsync(static_cast<T*>(w.V.ptr) + r, (size_t)b * sizeof(T),
-                                    static_cast<const T*>(w.basis[n].ptr) + r, (size_t)b * sizeof(T),
-                                    (size_t)(b - r) * sizeof(T), (size_t)M, cudaMemcpyDeviceToDevice, st));
-  }
+  // Start block [Y^T A_prev, previous Ritz vectors r..b] for a warm solve
+  // whose previous solve (the same mode in the previous sweep) had the same
+  // Gram shape: Y^T A_prev carries one power step on the new data, the
+  // previous Ritz vectors the next directions.  Otherwise [Y^T A_prev,
+  // random] (warm) or random (cold).
+  const bool have_prev = warm && w.basis_M[n] == M && w.basis_b[n] == b && b > r;
+  MACH_TRY(launch_start_block<T>(Y, static_cast<const T*>(w.fac[n].ptr), I, J, r, b, jroute, warm,
+                                 static_cast<T*>(w.V.ptr), static_cast<T*>(w.ytpart.ptr), 0x1000u + (uint32_t)n,
+                                 have_prev ? static_cast<const T*>(w.basis[n].ptr) : nullptr, st));
   w.basis_M[n] = M;
   w.basis_b[n] = b;
   EigLaunch e;

@@ -23,6 +23,23 @@ namespace mach {
 
 namespace {
 
+#ifdef MACH_EIG_PHASES
+// debugging aid: clock cycles of the fused eigensolver's phases, summed
+// over its launches (read with mach_debug_eig_phases in such a build)
+__device__ unsigned long long g_eig_phase[16];
+#define EIG_MARK(k)                                                              \
+  do {                                                                           \
+    __syncthreads();                                                             \
+    const long long t_ = clock64();                                              \
+    if (threadIdx.x == 0) atomicAdd(&g_eig_phase[k], (unsigned long long)(t_ - t_mark)); \
+    t_mark = t_;                                                                 \
+  } while (0)
+#else
+#define EIG_MARK(k) \
+  do {            \
+  } while (0)
+#endif
+
 constexpr int kEigThreads = 256;
 constexpr int kB = 32;        // maximum block width
 constexpr int kLd = kB + 1;   // padded leading dimension of b x b matrices
@@ -501,7 +518,7 @@ __device__ void final_rr(const T* U, const T* CU, int M, int ld, int r, T* Ur, d
     f.H[p * kRl + q] = 0.5 * (f.T1[p * kRl + q] + f.T1[q * kRl + p]);
   }
   __syncthreads();
-  rr_refine(f, r);
+  rr_refine(f, r, sizeof(T) == 4 ? 1e-5 : 1e-7);
   rr_write<T>(U, ld, M, r, f, Ur, Xr, theta);
 }
 
@@ -530,8 +547,12 @@ struct EigArgs {
 // ----------------------------------------------------------------------------
 // Fused path: one CTA, M <= kEigSmallMax.
 // ----------------------------------------------------------------------------
+
 template <typename T>
 __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, int smem_mode) {
+#ifdef MACH_EIG_PHASES
+  long long t_mark = clock64();
+#endif
   extern __shared__ __align__(16) unsigned char eig_smem[];
   __shared__ BSpace<T> bs;
   __shared__ FinalRR frr;
@@ -558,9 +579,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
   }
   if (threadIdx.x == 0) prev = 1e300;
   __syncthreads();
+  EIG_MARK(0);   // staging
   // orthonormalise the start block: P = V^T V, S from its scaled Cholesky
   grams_rows<T>(V, V, ld, b, 0, M, bs.P, nullptr, kLd);
   __syncthreads();
+  EIG_MARK(8);   // start Gram
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     col_scale_warp<T>(bs.P, b, bs.d);
@@ -580,6 +603,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     }
   }
   __syncthreads();
+  EIG_MARK(9);   // start Cholesky and solve (one warp)
   tile_gemm<T>(V, ld, bs.S, kLd, M, b, b, W, ld, nullptr);
   __syncthreads();
   {
@@ -590,16 +614,20 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
 
   int it = 0;
   bool conv = false;
+  EIG_MARK(1);   // start orthonormalisation
   for (; it < a.maxit; ++it) {
     tile_gemm<T>(C, ldc, V, ld, M, M, b, W, ld, nullptr);        // W = C V
     __syncthreads();
+    EIG_MARK(2);   // C V
     grams_rows<T>(V, W, ld, b, 0, M, bs.H, bs.P, kLd);           // H = V^T W, P = W^T W
     __syncthreads();
     tile_gemm<T>(V, ld, bs.H, kLd, M, b, b, U, ld, W);           // E = W - V H (U is free)
     __syncthreads();
     grams_rows<T>(U, U, ld, b, 0, M, bs.F, nullptr, kLd);        // F = E^T E
     __syncthreads();
+    EIG_MARK(3);   // b x b sums and the residual block
     bspace_step<T>(bs, b, r, a.tol, &prev, true, it + 1 == a.maxit);
+    EIG_MARK(4);   // b-space step
     if (bs.conv || it + 1 == a.maxit) {
       conv = bs.conv != 0;
       tile_gemm<T>(V, ld, bs.S, kLd, M, b, b, U, ld, nullptr);   // Ritz vectors
@@ -636,8 +664,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
       frr.G[p * kRl + q] = g;
     }
     __syncthreads();
-    rr_refine(frr, r);
+    EIG_MARK(5);   // Ritz vectors and basis out
+    rr_refine(frr, r, sizeof(T) == 4 ? 1e-5 : 1e-7);
+    EIG_MARK(6);   // FP64 refinement
     rr_write<T>(U, ld, M, r, frr, eig_out_u<T>(a.Vout, r), a.Vout, a.theta);
+    EIG_MARK(7);   // output
   } else {
     tile_gemm<T>(C, ldc, U, ld, M, M, r, W, ld, nullptr);        // C U_r
     __syncthreads();
@@ -772,6 +803,9 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
   // mode 1: iteration (next basis, or the Ritz rotation once converged);
   // mode 2: final (Ritz rotation)
   if (mode != 0 && split_done(ctl)) return;
+#ifdef MACH_EIG_PHASES
+  long long t_mark = clock64();
+#endif
   __shared__ BSpace<T> bs;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     T h = T(0), g = T(0);
@@ -816,6 +850,7 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
     }
   }
   __syncthreads();
+  EIG_MARK(10);   // split: partial sums (and the start Cholesky)
   bool final_rot = mode == 2;
   if (mode != 0) {
     __shared__ double prev;
@@ -877,7 +912,9 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
       prev = 1e300;
     }
     __syncthreads();
+    EIG_MARK(11);   // split: FP64 residual block
     bspace_step<T>(bs, b, r, check ? tol : 0.0, &prev, check, mode == 2);
+    EIG_MARK(12);   // split: b-space step
     if (check && bs.conv) final_rot = true;
     if (check && threadIdx.x == 0) ctl[2] = (unsigned long long)__double_as_longlong(prev);
   }
@@ -902,7 +939,8 @@ __global__ void __launch_bounds__(256) split_bspace_kernel(const T* part, int nb
       frr.G[p * kRl + q] = g;
     }
     __syncthreads();
-    rr_refine(frr, r);
+    rr_refine(frr, r, sizeof(T) == 4 ? 1e-5 : 1e-7);
+    EIG_MARK(13);   // split: final FP64 Rayleigh-Ritz
     // rr_out: X (r x r, columns in descending order of lambda), then lambda
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
       const int k = e / r, j = e - (e / r) * r;
@@ -957,6 +995,17 @@ __global__ void copy_kernel(const T* src, T* dst, int64_t n) {
 }  // namespace
 
 int eig_split_threshold() { return kEigSmallMax; }
+
+#ifdef MACH_EIG_PHASES
+extern "C" int mach_debug_eig_phases(unsigned long long* out8, int reset) {
+  if (cudaMemcpyFromSymbol(out8, g_eig_phase, sizeof(unsigned long long) * 16) != cudaSuccess) return 4;
+  if (reset) {
+    unsigned long long z[16] = {};
+    if (cudaMemcpyToSymbol(g_eig_phase, z, sizeof(z)) != cudaSuccess) return 4;
+  }
+  return 0;
+}
+#endif
 
 // split-path scratch: per-row-block partial Grams, the b x b transform S,
 // and the k-split partial tiles of C V

@@ -137,9 +137,9 @@ constexpr int kRRWarps = 8;   // warps of the CTAs that call rr_refine (256 thre
 // (lambda_j - lambda_i) for pairs separated by more than
 // delta = 2 (||offdiag S||_F + max|lambda| ||R||_F), R_ij / 2 otherwise,
 // and X <- X (I + E).  The error is squared by every round, so from a
-// start that is diagonal to FP32 precision one round reaches FP64
-// precision; when four rounds do not converge, a cyclic FP64 Jacobi on H
-// is used instead.  All threads of the CTA; one thread per entry.
+// start that is diagonal to FP32 precision one round reaches the FP32
+// paths' accuracy and two reach FP64 precision; when four rounds do not
+// converge, a cyclic FP64 Jacobi on H is used instead.  All threads of the CTA; one thread per entry.
 // ----------------------------------------------------------------------------
 constexpr int kRl = kMaxRank + 1;
 struct FinalRR {
@@ -151,7 +151,10 @@ struct FinalRR {
   int perm[kMaxRank];
 };
 
-__device__ void rr_refine(FinalRR& f, int r) {
+// `accept`: the round whose largest correction is below it is the last (the
+// remaining error is of the order of its square times the eigenvalue spread
+// over the smallest gap): 1e-5 for the FP32 paths, 1e-7 for FP64.
+__device__ void rr_refine(FinalRR& f, int r, double accept) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const bool act = tid < r * r;
   const int i = act ? tid / r : 0, j = act ? tid - (tid / r) * r : 0;
@@ -232,10 +235,7 @@ __device__ void rr_refine(FinalRR& f, int r) {
     }
     __syncthreads();
     if (act) f.X[i * kRl + j] = xn;
-    // the correction of this round was below 1e-6: the remaining error is
-    // of the order of its square (times the eigenvalue spread over the
-    // smallest gap), far below every tolerance of the paths
-    ok = f.emax < 1e-6;
+    ok = f.emax < accept;
     __syncthreads();
   }
   if (!ok) {

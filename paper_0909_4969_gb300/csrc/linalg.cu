@@ -106,11 +106,17 @@ __global__ void init_gram_kernel(const V* __restrict__ val, const uint16_t* __re
 // Starting blocks.  Deterministic pseudo-random fill (Philox of (i, j)) for
 // the columns not given by a warm start.
 // ----------------------------------------------------------------------------
+// Columns col0..b of the start block: the previous solve's Ritz vectors
+// (same M x b shape) when `prev` is given, else the pseudo-random fill.
 template <typename T>
-__global__ void fill_random_block(T* V, int M, int b, int col0, uint32_t salt) {
+__global__ void fill_random_block(T* V, int M, int b, int col0, uint32_t salt, const T* __restrict__ prev) {
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < M * b; o += gridDim.x * blockDim.x) {
     const int i = o / b, j = o - (o / b) * b;
     if (j < col0) continue;
+    if (prev) {
+      V[o] = prev[o];
+      continue;
+    }
     const uint4 w = philox4x32_10((uint32_t)i, (uint32_t)j, 0x4d414348u, salt);
     V[o] = (T)((double)w.x * (1.0 / 4294967296.0) - 0.5);
   }
@@ -315,6 +321,7 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
   }
   __syncwarp();
   for (int k = lane; k < rr; k += 32) rinv[k] = Ri[k];
+  if (lane == 0) *counter = 0u;   // ready for the next launch (it starts at zero with the sample)
 }
 
 // A = A64 R^-1: FP64 column-major output (I x r) and the row-major copy in T.
@@ -398,10 +405,10 @@ mach_status launch_init_gram(const void* val, const uint16_t* leaf, const uint32
 
 template <typename T>
 mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
-                               T* V, T* scratch, uint32_t salt, cudaStream_t st) {
+                               T* V, T* scratch, uint32_t salt, const T* prev_ritz, cudaStream_t st) {
   const int M = jroute ? J : I;
   fill_random_block<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024)),
-                         256, 0, st>>>(V, M, b, warm ? r : 0, salt);
+                         256, 0, st>>>(V, M, b, warm ? r : 0, salt, warm ? prev_ritz : nullptr);
   MACH_LAUNCH_CHECK();
   if (warm) {
     if (jroute) {
@@ -425,7 +432,8 @@ template <typename T>
 mach_status launch_lsv_finish(const T* Y, const EigResult<T>& ev, int I, int J, int r, bool jroute, double* A64,
                               double* gram64, unsigned* counter, double* rinv, unsigned* err, double* out_colmajor,
                               T* out_rowmajor, cudaStream_t st) {
-  MACH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+  // the completion counter is zero here: the sample's scalars start zeroed
+  // and the last CTA of every launch resets it
   // few partial Grams for the last CTA to sum: at most 64 CTAs, several rows per warp
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 32), 64));
   const size_t vbytes = (size_t)J * r * sizeof(T);
@@ -458,7 +466,7 @@ mach_status launch_core(const T* Y, const double* A, int I, int J, int r, double
 #define MACH_INST(T)                                                                                             \
   template mach_status launch_gram<T>(const T*, int64_t, int, int64_t, int64_t, T*, T*, int64_t, cudaStream_t);  \
   template mach_status launch_start_block<T>(const T*, const T*, int, int, int, int, bool, bool, T*, T*,       \
-                                             uint32_t, cudaStream_t);                                            \
+                                             uint32_t, const T*, cudaStream_t);                                  \
   template mach_status launch_lsv_finish<T>(const T*, const EigResult<T>&, int, int, int, bool, double*,        \
                                             double*, unsigned*, double*, unsigned*, double*, T*, cudaStream_t);  \
   template mach_status launch_factor_to_rowmajor<T>(const double*, int, int, T*, cudaStream_t);                  \

@@ -517,7 +517,7 @@ EigResult<T> eig_result(const EigLaunch& e);
 size_t eig_out_bytes(int M);
 template <typename T>
 mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
-                               T* V, T* scratch, uint32_t salt, cudaStream_t st);
+                               T* V, T* scratch, uint32_t salt, const T* prev_ritz, cudaStream_t st);
 template <typename T>
 mach_status launch_lsv_finish(const T* Y, const EigResult<T>& ev, int I, int J, int r, bool jroute,
                               double* A64, double* gram64, unsigned* counter, double* rinv, unsigned* err,

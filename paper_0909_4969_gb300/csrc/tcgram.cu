@@ -3,7 +3,7 @@
 // the mode-n matricization are the leading eigenvectors of this Gram).
 //
 // Every fibre along mode n is one column of X^_(n).  The fibres are taken
-// 32 at a time; a chunk of 32 fibres is written densely (zeros where the
+// 64 at a time; a chunk of 64 fibres is written densely (zeros where the
 // coin dropped the entry) into shared memory as BF16 operand tiles, and the
 // tile's outer product is accumulated by tcgen05.mma (kind::f16, BF16
 // operands, FP32 accumulators in tensor memory).  Where the sampled
@@ -39,15 +39,16 @@ namespace mach {
 
 namespace {
 
-constexpr int kTcK = 32;                         // fibres per chunk (MMA K per chunk)
+constexpr int kTcK = 64;                         // fibres per chunk (MMA K per chunk)
 constexpr int kTcRows = 256;                     // operand tile rows (two M = 128 MMAs)
 constexpr int kTcThreads = 256;
-constexpr uint32_t kTileBytes = kTcRows * kTcK * 2;   // 16 KB per BF16 tile
+constexpr uint32_t kTileBytes = kTcRows * kTcK * 2;   // 32 KB per BF16 tile
 constexpr uint32_t kLbo = 128;                   // K-adjacent core matrices
 constexpr uint32_t kSbo = (kTcK / 8) * 128;      // row-adjacent core matrices
 constexpr int kTcStages = 2;
 constexpr uint32_t kTmemCols = 512;
-constexpr size_t kTcSmem = 116 * 1024;           // > half the SM: one CTA per SM (it owns all 512 TMEM columns)
+constexpr size_t kTcSmem = 2 * 3 * kTileBytes;   // two stages of three tiles (192 KB): one CTA per SM, which owns
+                                                 // all 512 TMEM columns
 
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)(((row >> 3) * (kTcK / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gram_kernel(TcGramArgs a) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) uint64_t bar_mma[kTcStages];
   __shared__ uint32_t tmem_base_sh;
+  __shared__ uint32_t fst[kTcK + 1];   // entry offsets of the chunk's fibres (and the end)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nblk = a.nrb * a.nrb;
   const int blk = (int)(blockIdx.x % (unsigned)nblk), sp = (int)(blockIdx.x / (unsigned)nblk);
@@ -167,7 +169,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gram_kernel(TcGramArgs a) {
         break;
       }
     }
-    // zero the stage's tiles
+    // the chunk's fibre starts (one coalesced load, clamped past the last
+    // fibre), then zero the stage's tiles while they arrive
+    if (tid <= kTcK) {
+      const int64_t f = ch * kTcK + tid;
+      fst[tid] = a.fib_start[f < a.nfib ? f : a.nfib];
+    }
     {
       const int ntile = 1 + (shared_tile ? 0 : 1) + (a.terms == 2 ? 1 : 0);
       uint4* z = reinterpret_cast<uint4*>(st);
@@ -178,22 +185,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gram_kernel(TcGramArgs a) {
     unsigned char* tA = st;
     unsigned char* tB = shared_tile ? st : st + kTileBytes;
     unsigned char* tL = st + (shared_tile ? 1 : 2) * kTileBytes;
-    // scatter: warp w takes fibres w, w + 8, .. of the chunk, lanes its entries
-    for (int k = warp; k < kTcK; k += kTcThreads / 32) {
-      const int64_t f = ch * kTcK + k;
-      if (f >= a.nfib) break;
-      const uint32_t e0 = a.fib_start[f], e1 = a.fib_start[f + 1];
-      for (uint32_t e = e0 + lane; e < e1; e += 32) {
+    // scatter: the chunk's entries are contiguous; thread t takes entries
+    // t, t + 256, .. and finds its fibre (column k) by binary search in fst
+    {
+      const uint32_t s0 = fst[0], s1 = fst[kTcK];
+      for (uint32_t e = s0 + (uint32_t)tid; e < s1; e += kTcThreads) {
+        int lo = 0, hi = kTcK;   // fst[lo] <= e < fst[hi]
+#pragma unroll
+        for (int step = 0; step < 6; ++step) {
+          const int mid = (lo + hi) >> 1;
+          if (fst[mid] <= e) lo = mid;
+          else hi = mid;
+        }
+        const int k = lo;
         const int li = (int)a.leaf[e];
         const float x = load_val(a.val, a.vdt, e);
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const float lo = x - __bfloat162float(h);
+        const float lo_part = x - __bfloat162float(h);
         const unsigned ia = (unsigned)(li - r0), ib = (unsigned)(li - c0);
-        if (ia < (unsigned)kTcRows)
-          *reinterpret_cast<__nv_bfloat16*>(tA + tile_off((int)ia, k)) = h;
+        if (ia < (unsigned)kTcRows) *reinterpret_cast<__nv_bfloat16*>(tA + tile_off((int)ia, k)) = h;
         if (ib < (unsigned)kTcRows) {
           if (!shared_tile) *reinterpret_cast<__nv_bfloat16*>(tB + tile_off((int)ib, k)) = h;
-          if (a.terms == 2) *reinterpret_cast<__nv_bfloat16*>(tL + tile_off((int)ib, k)) = __float2bfloat16_rn(2.0f * lo);
+          if (a.terms == 2)
+            *reinterpret_cast<__nv_bfloat16*>(tL + tile_off((int)ib, k)) = __float2bfloat16_rn(2.0f * lo_part);
         }
       }
     }

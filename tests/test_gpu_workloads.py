@@ -35,18 +35,26 @@ def test_large_workload_full_size():
     w = synth.config_large_fp32(1000)
     ranks = w.spec.ranks
     X, _, _ = synth.tucker_torch(w.spec, device="cuda")
+    # X is written on the default stream and read on another: finish it first
+    torch.cuda.synchronize()
     st = torch.cuda.Stream()
+    x_sum0 = float(torch.sum(X, dtype=torch.float64))
     with torch.cuda.stream(st):
         s = mach.sample(X, w.p, w.spec.seed)
         idx = s.indices().cpu().numpy()
+        vals = s.values().cpu().numpy()
         G32, A32 = s.hooi(ranks, w.sweeps, "fp32")
         G64, A64 = s.hooi(ranks, w.sweeps, "fp64")
         st.synchronize()
         assert s.stats()["flags"] == 0
         s.free()
+    x_sum1 = float(torch.sum(X, dtype=torch.float64))
     Xh = X.cpu().numpy()
     del X
     torch.cuda.empty_cache()
+    # the input is untouched by the decompositions, and the sample holds its values
+    assert x_sum0 == x_sum1, (x_sum0, x_sum1)
+    assert np.array_equal(vals, Xh.reshape(-1)[idx]), "sampled values differ from the input's"
     S, G_o, A_o = O.mach_hooi(Xh, ranks, w.p, w.spec.seed, w.sweeps)
     assert np.array_equal(idx, S.idx), "sampled index set differs from the oracle"
     dec = {"fp32": (G32.cpu().numpy(), [a.cpu().numpy() for a in A32]),
