@@ -183,10 +183,12 @@ __global__ void copy_cols(const T* __restrict__ A, int M, int r, T* V, int b) {
 // U_r X, formed here (FP64 work spread over the CTAs):
 //  J-route: A64[i][k] = sum_m (sum_j Y[i][j] U_r[j][m]) X[m][k] / sqrt(theta_k)
 //  I-route: A64[i][k] = sum_m U_r[i][m] X[m][k].
-// Then FP64 Cholesky QR: every CTA writes its partial Gram A_blk^T A_blk to
-// part[blockIdx] (register accumulation per lane, warp partials reduced in
-// shared memory); the last CTA to finish sums the partials in block order
-// (deterministic), factors G = R^T R and stores R^-1 (upper) in rinv.
+// Then the FP64 re-orthonormalisation A <- A Z: every CTA writes its
+// partial Gram A_blk^T A_blk to part[blockIdx] (register accumulation per
+// lane, warp partials reduced in shared memory); the last CTA to finish sums
+// the partials in block order (deterministic) and stores Z in rinv: the
+// series G^-1/2 when G is within 1e-4 of the identity (always, for
+// converged eigenvectors), else R^-1 of the Cholesky factor G = R^T R.
 // ----------------------------------------------------------------------------
 constexpr int kPairsPerLane = (kMaxRank * kMaxRank + 31) / 32;
 constexpr size_t kLsvStageBytes = 48 * 1024;
@@ -292,8 +294,40 @@ __global__ void __launch_bounds__(256) lsv_apply_kernel(const T* __restrict__ Y,
     G[e] = t;
   }
   __syncthreads();
+  // The rows are orthonormal up to the eigenvectors' accuracy and rounding,
+  // so E = G - I is small: then the symmetric orthonormalisation
+  // G^-1/2 = I - E/2 + 3/8 E^2 (the binomial series; the first omitted term,
+  // 5/16 E^3, is below 4e-13 for max |E_ij| <= 1e-4) takes three parallel
+  // steps instead of the serial FP64 Cholesky.
+  __shared__ double emax_w[8];
+  {
+    double em = 0.0;
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+      const int p = e / r, q = e - (e / r) * r;
+      em = fmax(em, fabs(G[e] - (p == q ? 1.0 : 0.0)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if (lane == 0) emax_w[warp] = em;
+  }
+  __syncthreads();
+  double emax = 0.0;
+  for (int w = 0; w < nw; ++w) emax = fmax(emax, emax_w[w]);
+  if (emax <= 1e-4) {
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+      const int p = e / r, q = e - (e / r) * r;
+      double e2 = 0.0;
+      for (int k = 0; k < r; ++k)
+        e2 += (G[p * r + k] - (p == k ? 1.0 : 0.0)) * (G[k * r + q] - (k == q ? 1.0 : 0.0));
+      const double epq = G[e] - (p == q ? 1.0 : 0.0);
+      rinv[e] = (p == q ? 1.0 : 0.0) - 0.5 * epq + 0.375 * e2;
+    }
+    if (threadIdx.x == 0) *counter = 0u;   // ready for the next launch
+    return;
+  }
   if (warp != 0) return;
-  // upper Cholesky G = R^T R in place (one warp, lane c owns column c)
+  // otherwise: upper Cholesky G = R^T R in place (one warp, lane c owns
+  // column c) and A R^-1
   for (int j = 0; j < r; ++j) {
     double djj = G[j * r + j];
     if (!(djj > 0.0)) {
@@ -332,7 +366,7 @@ __global__ void lsv_finish_kernel(const double* __restrict__ A64, const double* 
   if (o >= I * r) return;
   const int i = o / r, k = o - (o / r) * r;
   double s = 0.0;
-  for (int j = 0; j <= k; ++j) s += A64[(size_t)i * r + j] * rinv[j * r + k];
+  for (int j = 0; j < r; ++j) s += A64[(size_t)i * r + j] * rinv[j * r + k];
   out_colmajor[(size_t)k * I + i] = s;
   out_rowmajor[(size_t)i * r + k] = (T)s;
 }
