@@ -162,25 +162,52 @@ __device__ void rr_refine(FinalRR& f, int r, double accept) {
   __syncthreads();
   bool ok = false;
   for (int round = 0; round < 4 && !ok; ++round) {
-    if (act) {
-      double a = 0.0, g = 0.0;
-      for (int k = 0; k < r; ++k) {
-        const double x = f.X[k * kRl + j];
-        a += f.H[i * kRl + k] * x;
-        g += f.G[i * kRl + k] * x;
-      }
-      f.T1[i * kRl + j] = a;   // H X
-      f.T2[i * kRl + j] = g;   // G X
-    }
-    __syncthreads();
     double sx = 0.0, rx = 0.0;
-    if (act) {
-      for (int k = 0; k < r; ++k) {
-        const double x = f.X[k * kRl + i];
-        sx += x * f.T1[k * kRl + j];
-        rx += x * f.T2[k * kRl + j];
+    if (round == 0) {
+      // X = I: S = H and R = I - G, no products
+      if (act) {
+        sx = f.H[i * kRl + j];
+        rx = (i == j ? 1.0 : 0.0) - f.G[i * kRl + j];
       }
-      rx = (i == j ? 1.0 : 0.0) - rx;
+    } else {
+      // two partial sums per product: FP64 dependences are long on this part
+      if (act) {
+        double a0 = 0.0, a1 = 0.0, g0 = 0.0, g1 = 0.0;
+        int k = 0;
+        for (; k + 1 < r; k += 2) {
+          const double x0 = f.X[k * kRl + j], x1 = f.X[(k + 1) * kRl + j];
+          a0 += f.H[i * kRl + k] * x0;
+          g0 += f.G[i * kRl + k] * x0;
+          a1 += f.H[i * kRl + k + 1] * x1;
+          g1 += f.G[i * kRl + k + 1] * x1;
+        }
+        if (k < r) {
+          const double x0 = f.X[k * kRl + j];
+          a0 += f.H[i * kRl + k] * x0;
+          g0 += f.G[i * kRl + k] * x0;
+        }
+        f.T1[i * kRl + j] = a0 + a1;   // H X
+        f.T2[i * kRl + j] = g0 + g1;   // G X
+      }
+      __syncthreads();
+      if (act) {
+        double s0 = 0.0, s1 = 0.0, r0 = 0.0, r1 = 0.0;
+        int k = 0;
+        for (; k + 1 < r; k += 2) {
+          const double x0 = f.X[k * kRl + i], x1 = f.X[(k + 1) * kRl + i];
+          s0 += x0 * f.T1[k * kRl + j];
+          r0 += x0 * f.T2[k * kRl + j];
+          s1 += x1 * f.T1[(k + 1) * kRl + j];
+          r1 += x1 * f.T2[(k + 1) * kRl + j];
+        }
+        if (k < r) {
+          const double x0 = f.X[k * kRl + i];
+          s0 += x0 * f.T1[k * kRl + j];
+          r0 += x0 * f.T2[k * kRl + j];
+        }
+        sx = s0 + s1;
+        rx = (i == j ? 1.0 : 0.0) - (r0 + r1);
+      }
     }
     __syncthreads();
     if (act) {
@@ -196,14 +223,15 @@ __device__ void rr_refine(FinalRR& f, int r, double accept) {
       f.red[1][warp] = q;
     }
     __syncthreads();
-    if (tid == 0) {
-      double so = 0.0, sr = 0.0, lm = 0.0;
-      for (int w = 0; w < nw; ++w) {
-        so += f.red[0][w];
-        sr += f.red[1][w];
-      }
-      for (int k = 0; k < r; ++k) lm = fmax(lm, fabs(f.lam[k]));
-      f.delta = 2.0 * (sqrt(so) + lm * sqrt(sr));
+    if (warp == 0) {
+      // warp-parallel sums over the warps and maximum over lambda
+      double so = lane < nw ? f.red[0][lane] : 0.0, sr = lane < nw ? f.red[1][lane] : 0.0;
+      double lm = lane < r ? fabs(f.lam[lane]) : 0.0;
+      so = warp_sum(so);
+      sr = warp_sum(sr);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, d));
+      if (lane == 0) f.delta = 2.0 * (sqrt(so) + lm * sqrt(sr));
     }
     __syncthreads();
     double e = 0.0;
@@ -222,16 +250,23 @@ __device__ void rr_refine(FinalRR& f, int r, double accept) {
     if (lane == 0) f.red[2][warp] = em;
     __syncthreads();
     if (act) f.T1[i * kRl + j] = e;   // E (S no longer needed)
-    if (tid == 0) {
-      double m = 0.0;
-      for (int w = 0; w < nw; ++w) m = fmax(m, f.red[2][w]);
-      f.emax = m;
+    if (warp == 0) {
+      double m = lane < nw ? f.red[2][lane] : 0.0;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+      if (lane == 0) f.emax = m;
     }
     __syncthreads();
     double xn = 0.0;
     if (act) {
-      xn = f.X[i * kRl + j];
-      for (int k = 0; k < r; ++k) xn += f.X[i * kRl + k] * f.T1[k * kRl + j];
+      double x0 = f.X[i * kRl + j], x1 = 0.0;
+      int k = 0;
+      for (; k + 1 < r; k += 2) {
+        x0 += f.X[i * kRl + k] * f.T1[k * kRl + j];
+        x1 += f.X[i * kRl + k + 1] * f.T1[(k + 1) * kRl + j];
+      }
+      if (k < r) x0 += f.X[i * kRl + k] * f.T1[k * kRl + j];
+      xn = x0 + x1;
     }
     __syncthreads();
     if (act) f.X[i * kRl + j] = xn;

@@ -77,7 +77,10 @@ __global__ void sum_partials_kernel(const T* __restrict__ part, int nsplit, int6
 // ----------------------------------------------------------------------------
 // HOSVD Gram C = X^_(n) X^_(n)^T (raw values) from the fibres along mode n
 // (every fibre is one column of the mode-n matricization): C[a][b] +=
-// x_a x_b for every pair of entries of a fibre.  One warp per fibre.
+// x_a x_b for every pair of entries of a fibre.  One warp per fibre, the
+// lanes over its unordered pairs (one FP atomic each, into the upper
+// triangle: half the atomics of adding both C[a][b] and C[b][a]), then one
+// pass mirrors the upper triangle.
 // ----------------------------------------------------------------------------
 template <typename V, typename T>
 __global__ void init_gram_kernel(const V* __restrict__ val, const uint16_t* __restrict__ leaf,
@@ -89,16 +92,31 @@ __global__ void init_gram_kernel(const V* __restrict__ val, const uint16_t* __re
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t f = gw; f < nfib; f += nw) {
     const uint32_t s0 = fib_start[f], s1 = fib_start[f + 1];
-    for (uint32_t i = s0 + lane; i < s1; i += 32) {
-      const uint32_t a = leaf[i];
-      const T vi = (T)val[i];
-      for (uint32_t j = i; j < s1; ++j) {
-        const uint32_t b = leaf[j];
-        const T v = vi * (T)val[j];
-        atomicAdd(&C[(size_t)a * M + b], v);
-        if (a != b) atomicAdd(&C[(size_t)b * M + a], v);
+    const uint32_t n = s1 - s0, npair = n * (n + 1) / 2;
+    // the fibre's unordered pairs (i <= j) spread over the lanes; one atomic
+    // per pair into the upper triangle (gram_symmetrize_kernel mirrors it)
+    for (uint32_t k0 = lane; k0 < npair; k0 += 32) {
+      uint32_t i = 0, k = k0;
+      while (k >= n - i) {
+        k -= n - i;
+        ++i;
       }
+      const uint32_t j = i + k;
+      const uint32_t a = leaf[s0 + i], b2 = leaf[s0 + j];
+      const T v = (T)val[s0 + i] * (T)val[s0 + j];
+      const uint32_t lo = a < b2 ? a : b2, hi = a < b2 ? b2 : a;
+      atomicAdd(&C[(size_t)lo * M + hi], v);
     }
+  }
+}
+
+// C[hi][lo] = C[lo][hi] for lo < hi.
+template <typename T>
+__global__ void gram_symmetrize_kernel(T* __restrict__ C, int M) {
+  const int64_t n = (int64_t)M * M;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(o / M), c = (int)(o - (o / M) * M);
+    if (r > c) C[o] = C[(size_t)c * M + r];
   }
 }
 
@@ -431,6 +449,8 @@ mach_status launch_init_gram(const void* val, const uint16_t* leaf, const uint32
   const int64_t warps = std::max<int64_t>(1, std::min<int64_t>(nfib_cap, (int64_t)num_sms() * 64));
   init_gram_kernel<V, T><<<(unsigned)ceil_div(warps * 32, threads), threads, 0, st>>>(
       static_cast<const V*>(val), leaf, fib_start, d_nfib, M, C);
+  MACH_LAUNCH_CHECK();
+  gram_symmetrize_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div((int64_t)M * M, 256), 4096), 256, 0, st>>>(C, M);
   MACH_LAUNCH_CHECK();
   return MACH_OK;
 }
