@@ -290,8 +290,14 @@ struct BSpace {
 template <typename T>
 __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev, bool check, bool final_rotation) {
   const int tid = threadIdx.x, lane = tid & 31;
+  // The Ritz rotation of an FP32 iteration that neither tests convergence
+  // nor ends the solve only orients the next basis (span(C V) does not
+  // depend on it, and the scaled Cholesky QR needs W S only roughly
+  // orthogonal): three Jacobi sweeps there, full accuracy on testing and
+  // final iterations.
+  const int sweeps = sizeof(T) == 8 ? 12 : (check || final_rotation ? 8 : 3);
   if (tid < 32) {
-    jacobi_warp<T>(s.H, s.Q, b, sizeof(T) == 8 ? T(1e-14) : T(1e-6), sizeof(T) == 8 ? 12 : 8);
+    jacobi_warp<T>(s.H, s.Q, b, sizeof(T) == 8 ? T(1e-14) : T(1e-6), sweeps);
     sort_desc_warp<T>(s.H, b, s.perm);
     if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
   }
