@@ -295,18 +295,55 @@ __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev
   // depend on it, and the scaled Cholesky QR needs W S only roughly
   // orthogonal): three Jacobi sweeps there, full accuracy on testing and
   // final iterations.
-  const int sweeps = sizeof(T) == 8 ? 12 : (check || final_rotation ? 8 : 3);
-  if (tid < 32) {
-    jacobi_warp<T>(s.H, s.Q, b, sizeof(T) == 8 ? T(1e-14) : T(1e-6), sweeps);
-    sort_desc_warp<T>(s.H, b, s.perm);
-    if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
+  //
+  // FP64: FP64 runs at 1/64 of FP32 on this part and a Jacobi sweep of the
+  // b x b problem is ~6 b^3 dependent-round FP64 operations on one warp, so
+  // every iteration rotates by an FP32 Jacobi of a scaled, rounded copy of H
+  // (the rotation is exact in FP64 as a matrix; the next basis is
+  // re-orthonormalised in FP64 and its span does not depend on the
+  // rotation), and only the rotation that is kept (converged or last
+  // iteration) is recomputed by the FP64 Jacobi below.
+  if (sizeof(T) == 8) {
+    float* Hf = reinterpret_cast<float*>(s.G);   // G is scratch until the residual test
+    float* Qf = Hf + kB * kLd;
+    if (tid < 32) {
+      T hm = lane < b ? fabs(s.H[lane * kLd + lane]) : T(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+      if (lane == 0) s.d[0] = hm > T(0) ? T(1) / hm : T(1);   // d is free until the next basis
+    }
+    __syncthreads();
+    const T sc = s.d[0];
+    for (int e = tid; e < b * b; e += blockDim.x) {
+      const int a = e / b, j = e - a * b;
+      Hf[a * kLd + j] = (float)(s.H[a * kLd + j] * sc);
+    }
+    __syncthreads();
+    if (tid < 32) {
+      jacobi_warp<float>(Hf, Qf, b, 1e-6f, 8);
+      sort_desc_warp<float>(Hf, b, s.perm);
+      if (lane < b) s.theta[lane] = (T)Hf[s.perm[lane] * kLd + s.perm[lane]] / sc;
+    }
+    __syncthreads();
+    for (int e = tid; e < b * b; e += blockDim.x) {
+      const int a = e / b, j = e - a * b;
+      s.S[a * kLd + j] = (T)Qf[a * kLd + s.perm[j]];
+    }
+    __syncthreads();
+  } else {
+    const int sweeps = check || final_rotation ? 8 : 3;
+    if (tid < 32) {
+      jacobi_warp<T>(s.H, s.Q, b, T(1e-6), sweeps);
+      sort_desc_warp<T>(s.H, b, s.perm);
+      if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
+    }
+    __syncthreads();
+    for (int e = tid; e < b * b; e += blockDim.x) {
+      const int a = e / b, j = e - a * b;
+      s.S[a * kLd + j] = s.Q[a * kLd + s.perm[j]];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < b * b; e += blockDim.x) {
-    const int a = e / b, j = e - a * b;
-    s.S[a * kLd + j] = s.Q[a * kLd + s.perm[j]];
-  }
-  __syncthreads();
   if (check) {
     // res_j^2 = q_j^T F q_j for the leading r Ritz pairs
     for (int e = tid; e < b * r; e += blockDim.x) {
@@ -338,6 +375,20 @@ __device__ void bspace_step(BSpace<T>& s, int b, int r, double tol, double* prev
     s.conv = 0;
   }
   __syncthreads();
+  if (sizeof(T) == 8 && (s.conv || final_rotation)) {
+    // the kept rotation in full FP64 precision (H is still unrotated)
+    if (tid < 32) {
+      jacobi_warp<T>(s.H, s.Q, b, T(1e-14), 12);
+      sort_desc_warp<T>(s.H, b, s.perm);
+      if (lane < b) s.theta[lane] = s.H[s.perm[lane] * kLd + s.perm[lane]];
+    }
+    __syncthreads();
+    for (int e = tid; e < b * b; e += blockDim.x) {
+      const int a = e / b, j = e - a * b;
+      s.S[a * kLd + j] = s.Q[a * kLd + s.perm[j]];
+    }
+    __syncthreads();
+  }
   if (s.conv || final_rotation) return;
   // G = P S, then F = S^T G (F is free once the residual is taken)
   for (int e = tid; e < b * b; e += blockDim.x) {
