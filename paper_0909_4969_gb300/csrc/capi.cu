@@ -295,9 +295,11 @@ Cyc cyc(int d, int n) {
 int block_size_for(int M, int r, bool cold, bool fp64) {
   // warm starts (previous factor + previous Ritz directions) need few
   // iterations, so the block carries only a few guard directions past r;
-  // cold starts carry more (FP64 results are compared at 1e-10, so the
-  // widest block there)
-  int b = cold ? (fp64 ? 32 : std::max(2 * r + 4, 24)) : std::max(r + 6, 16);
+  // FP64 cold starts carry the widest block (their results are compared at
+  // 1e-10); FP32 cold starts the warm width: the b-space step, whose Jacobi
+  // costs ~b^3 per sweep on one warp, bounds the multi-CTA route, and the
+  // HOOI sweeps refine the start
+  int b = cold && fp64 ? 32 : std::max(r + 6, 16);
   b = std::min(b, 32);
   return std::min(b, M);
 }
