@@ -144,7 +144,7 @@ __global__ void fill_random_block(T* V, int M, int b, int col0, uint32_t salt, c
 // row-major T): CTA (jb, sp) handles columns [32 jb, 32 jb + 32) of Y over the
 // rows i = sp, sp + nsplit, ..; threads (tx, ty): tx = column, ty = row
 // phase; coalesced reads of Y rows, A rows broadcast.  Partials land in
-// part[sp][j][k] and are summed in split order by yt_reduce (deterministic).
+// part[sp][j][k] and are summed in split order by yt_reduce_fill (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(256) yt_times_a_part(const T* __restrict__ Y, const T* __restrict__ A, int I,
                                                        int J, int r, int nsplit, T* __restrict__ part) {
@@ -176,14 +176,25 @@ __global__ void __launch_bounds__(256) yt_times_a_part(const T* __restrict__ Y, 
   }
 }
 
+// The whole warm J-route start block in one pass: columns 0..r the sum of
+// the Y^T A partials in split order, columns r..b the previous Ritz vectors
+// (or the pseudo-random fill).
 template <typename T>
-__global__ void yt_reduce(const T* __restrict__ part, int nsplit, int J, int r, T* __restrict__ V, int b) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= J * r) return;
-  const int j = o / r, k = o - (o / r) * r;
-  T s = T(0);
-  for (int sp = 0; sp < nsplit; ++sp) s += part[(size_t)sp * J * r + o];
-  V[(size_t)j * b + k] = s;
+__global__ void yt_reduce_fill(const T* __restrict__ part, int nsplit, int J, int r, T* __restrict__ V, int b,
+                               uint32_t salt, const T* __restrict__ prev) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < J * b; o += gridDim.x * blockDim.x) {
+    const int j = o / b, k = o - (o / b) * b;
+    if (k < r) {
+      T s = T(0);
+      for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * J + j) * r + k];
+      V[o] = s;
+    } else if (prev) {
+      V[o] = prev[o];
+    } else {
+      const uint4 w = philox4x32_10((uint32_t)j, (uint32_t)k, 0x4d414348u, salt);
+      V[o] = (T)((double)w.x * (1.0 / 4294967296.0) - 0.5);
+    }
+  }
 }
 
 template <typename T>
@@ -461,9 +472,11 @@ template <typename T>
 mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, int b, bool jroute, bool warm,
                                T* V, T* scratch, uint32_t salt, const T* prev_ritz, cudaStream_t st) {
   const int M = jroute ? J : I;
-  fill_random_block<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024)),
-                         256, 0, st>>>(V, M, b, warm ? r : 0, salt, warm ? prev_ritz : nullptr);
-  MACH_LAUNCH_CHECK();
+  const unsigned fill_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)M * b, 256), 1024));
+  if (!(warm && jroute)) {
+    fill_random_block<T><<<fill_grid, 256, 0, st>>>(V, M, b, warm ? r : 0, salt, warm ? prev_ritz : nullptr);
+    MACH_LAUNCH_CHECK();
+  }
   if (warm) {
     if (jroute) {
       // partials (nsplit x J x r) live in `scratch` (>= 64 J kMaxRank elements)
@@ -473,7 +486,7 @@ mach_status launch_start_block(const T* Y, const T* Aprev, int I, int J, int r, 
       yt_times_a_part<T><<<dim3((unsigned)ceil_div(J, 32), (unsigned)nsplit), 256, 0, st>>>(Y, Aprev, I, J, r, nsplit,
                                                                                            part);
       MACH_LAUNCH_CHECK();
-      yt_reduce<T><<<(unsigned)ceil_div((int64_t)J * r, 128), 128, 0, st>>>(part, nsplit, J, r, V, b);
+      yt_reduce_fill<T><<<fill_grid, 256, 0, st>>>(part, nsplit, J, r, V, b, salt, prev_ritz);
     } else {
       copy_cols<T><<<(unsigned)ceil_div((int64_t)I * r, 128), 128, 0, st>>>(Aprev, I, r, V, b);
     }
