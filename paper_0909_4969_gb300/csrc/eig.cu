@@ -675,8 +675,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_fused_kernel(EigArgs<T> a, in
     col_scale_warp<T>(bs.P, b, bs.d);
     if (lane < b)
       for (int j = 0; j < b; ++j) bs.G[lane * kLd + j] = bs.P[lane * kLd + j] * bs.d[lane] * bs.d[j];
-    // A warm start block ([Y^T A_prev, previous Ritz directions]) is nearly
-    // orthonormal once its columns are scaled: with E = D P D - I and
+    // A warm start block ([Y^T A_prev, previous Ritz directions]) can be
+    // nearly orthonormal once its columns are scaled: with E = D P D - I and
     // ||E||_F small, S = D (I + E)^-1/2 = D (I - E/2 + 3/8 E^2) (the
     // omitted terms are below 5/16 ||E||_F^3: 3e-7 at the FP32 threshold
     // 1e-2, 3e-16 at the FP64 threshold 1e-5) takes one parallel product
