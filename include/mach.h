@@ -53,13 +53,16 @@ typedef enum mach_status {
 typedef enum mach_dtype { MACH_F32 = 0, MACH_F64 = 1 } mach_dtype;
 
 /* Arithmetic of the HOOI sweep.  FP64: every contraction, Gram, eigensolve
- * and QR in FP64.  FP32: tensor-times-matrix chain and Gram in FP32 with FP32
- * accumulation; the R x R eigensolve and the QR re-orthonormalisation in
- * FP64.  BF16_REFINE: the requested sweeps read BF16 copies of the sampled
- * values (chain in FP32 accumulation), then three more sweeps with the input
- * values refine the factors (subspace iteration from the BF16 solution; the
- * core is formed from the input values); the small eigensolve and QR in
- * FP64. */
+ * and re-orthonormalisation in FP64 (the small b x b rotations of the
+ * intermediate subspace iterations are found in FP32, as they only orient
+ * the next basis; the rotation that is kept is computed in FP64).  FP32:
+ * tensor-times-matrix chain and Gram in FP32 with FP32 accumulation; the
+ * R x R eigensolve and the re-orthonormalisation of the factors in FP64.
+ * BF16_REFINE: the requested sweeps read BF16 copies of the sampled values
+ * (chain in FP32 accumulation), then three more sweeps with the input values
+ * refine the factors (subspace iteration from the BF16 solution; the core is
+ * formed from the input values); the small eigensolve and the
+ * re-orthonormalisation in FP64. */
 typedef enum mach_prec {
   MACH_PREC_FP64 = 0,
   MACH_PREC_FP32 = 1,
